@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of the integral-direct, Schwarz-screened J/K build (the hot path of the Hartree-Fock
+energy functional H(P)) on synthetic water clusters.
+
+One step = one J/K build of the workload's density: every unique shell quartet that passes
+Schwarz screening (tau = 1e-10) is evaluated (Boys, Obara-Saika VRR, contraction, HGP HRR) and
+digested into J and K, then J and K are symmetrised.  Metric: unique Cartesian function quartets
+per second (after screening) in the reduced-precision mode, whose energy error against the FP64
+path is reported beside it (bar: <= 1e-6 Ha); the plain FP64 path is timed on the same input.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload water8]
+
+N > 1 runs under torchrun: independent replicas of the workload, one per GPU (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "water8": dict(nwater=8, box=12.0, seed=2002, basis="6-31gs",
+                   desc="(H2O)_8 cluster, seed 2002, O uniform in a 12-bohr cube, O-O >= 5 bohr, 6-31G* (152 functions)"),
+    "water32": dict(nwater=32, box=19.0, seed=2006, basis="6-31gs",
+                    desc="(H2O)_32 cluster, seed 2006, 19-bohr cube, O-O >= 5 bohr, 6-31G* (608 functions)"),
+}
+METRIC = "Schwarz-screened ERI quartets/s and SCF molecules/s vs plain FP64, at <=1e-6 Ha"
+UNIT = "unique function quartets/s"
+SCHWARZ_TAU = 1e-10
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _build_library():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def _workload(name):
+    import mess_inputs as mi
+    w = WORKLOADS[name]
+    mol = mi.water_cluster(w["nwater"], w["box"], w["seed"])
+    return mol, mi.basis_path(w["basis"]), w
+
+
+def _scf_density(g, iters=60):
+    """Input preparation: a converged closed-shell density from Roothaan iterations whose J/K come
+    from the library's FP64 path (not timed)."""
+    import numpy as np
+    S, H = g.overlap(), g.kinetic() + g.nuclear()
+    s, U = np.linalg.eigh(S)
+    X = U @ np.diag(s ** -0.5) @ U.T
+    nocc = g.nelectron // 2
+
+    def dens(F):
+        _, C = np.linalg.eigh(X.T @ F @ X)
+        C = X @ C
+        return 2.0 * C[:, :nocc] @ C[:, :nocc].T
+
+    D, Fs, es, E_old = dens(H), [], [], 0.0
+    for _ in range(iters):
+        J, K, _ = g.jk(D, prec="fp64", schwarz_tau=SCHWARZ_TAU)
+        F = H + J - 0.5 * K
+        E = 0.5 * float(np.sum(D * (H + F)))
+        err = F @ D @ S - S @ D @ F
+        if abs(E - E_old) < 1e-9 and np.abs(err).max() < 1e-7:
+            break
+        E_old = E
+        Fs, es = (Fs + [F])[-8:], (es + [err])[-8:]
+        if len(Fs) >= 2:
+            k = len(Fs)
+            B = -np.ones((k + 1, k + 1))
+            B[-1, -1] = 0.0
+            for i in range(k):
+                for j in range(k):
+                    B[i, j] = float(np.sum(es[i] * es[j]))
+            c = np.linalg.solve(B, np.r_[np.zeros(k), -1.0])[:k]
+            F = sum(ci * Fi for ci, Fi in zip(c, Fs))
+        D = dens(F)
+    return D
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock / throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.device_index is not None:
+                cmd += ["-i", str(self.device_index)]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def _nvsmi_index(torch, local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",")]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    try:
+        u = str(torch.cuda.get_device_properties(local_rank).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return local_rank
+
+
+def _oracle_rate(mol, basis_path, nelem, seed=7):
+    """The FP64 CPU oracle as it stands: nelem sampled J/K elements of the workload by their
+    defining sums over all (l, s) (every integral evaluated, no screening); returns (integral
+    evaluations per second, threads, seconds)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    o = oracle.basis_for(mol, basis_path)
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, o.nfn, nelem)
+    cols = rng.integers(0, o.nfn, nelem)
+    D = np.eye(o.nfn)
+    t0 = time.perf_counter()
+    oracle.jk_elements(o, D, rows, cols)
+    dt = time.perf_counter() - t0
+    evals = 2 * nelem * o.nfn * o.nfn       # one integral per (l, s) for J and for K
+    return evals / dt, oracle.num_threads(), dt
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    mol, bpath, w = _workload(args.workload)
+    per_step = 16
+    for _ in range(args.warmup):
+        _oracle_rate(mol, bpath, per_step)
+    rates, total = [], 0.0
+    for k in range(args.steps):
+        r, threads, dt = _oracle_rate(mol, bpath, per_step, seed=100 + k)
+        rates.append(r)
+        total += dt
+    value = sum(rates) / len(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": w["desc"], "schwarz_tau": SCHWARZ_TAU,
+                   "l2": "host CPU run"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} sampled J/K elements per step, each by its defining sum over "
+                                   f"all (l, s) (2 n^2 integral evaluations per element, one function quartet each)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local_rank = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        _build_library()
+    if dist:
+        dist.barrier(device_ids=[local_rank])
+    import paper_2406_03121_gb300 as mess
+
+    mol, bpath, w = _workload(args.workload)
+    g = mess.Basis.from_molecule(mol, bpath)
+    n = g.nbf
+    D = _scf_density(g)
+    dev = torch.device("cuda", local_rank)
+    dD = torch.from_numpy(D).to(dev)
+    dJ, dK = torch.empty_like(dD), torch.empty_like(dD)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    kw = dict(prec=args.prec, schwarz_tau=SCHWARZ_TAU, fp64_tau=args.fp64_tau, stream=stream)
+
+    def timed(nsteps, **over):
+        opts = dict(kw, **over)
+        tot, info = 0.0, None
+        for _ in range(nsteps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = g.jk_device(dD, dJ, dK, **opts)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot, info
+
+    for _ in range(args.warmup):
+        g.jk_device(dD, dJ, dK, **kw)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(_nvsmi_index(torch, local_rank))
+    clocks.start()
+    if dist:
+        dist.barrier(device_ids=[local_rank])
+    torch.cuda.synchronize(dev)
+    total_ms, info = timed(args.steps)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier(device_ids=[local_rank])
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    fnq = info["function_quartets"]
+    value = world * fnq * args.steps / (max_ms * 1e-3)
+    J_mix, K_mix = dJ.cpu().numpy(), dK.cpu().numpy()
+
+    # plain FP64 path on the same input, and the energy error of the reduced-precision path
+    fp64_steps = max(2, min(args.steps, 5))
+    for _ in range(1):
+        g.jk_device(dD, dJ, dK, **dict(kw, prec="fp64"))
+    ms64, info64 = timed(fp64_steps, prec="fp64")
+    J64, K64 = dJ.cpu().numpy(), dK.cpu().numpy()
+    e2 = lambda J, K: 0.5 * float(np.sum(D * (J - 0.5 * K)))  # noqa: E731
+    dE = e2(J_mix, K_mix) - e2(J64, K64)
+    fp64_rate = info64["function_quartets"] * fp64_steps / (ms64 * 1e-3)
+
+    # roofline of the dominant kernel: per-launch CUDA events on the launching stream
+    prof = None
+    for _ in range(3):
+        parts = g.jk_profile(dD, dJ, dK, **kw)
+        if prof is None:
+            prof = [dict(p, ms=[p["ms"]]) for p in parts]
+        else:
+            for acc, p in zip(prof, parts):
+                acc["ms"].append(p["ms"])
+    for p in prof:
+        p["ms"] = statistics.mean(p["ms"])
+    dom = max(prof, key=lambda p: p["ms"])
+    fp32_peak, fp64_peak = mess.fma_peak(stream)
+    peak = fp64_peak if dom["fp64"] else fp32_peak
+    achieved = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+    tot_flops = sum(p["flops"] for p in prof)
+    tot_ms = sum(p["ms"] for p in prof)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "jk_dram_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            key = f"{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']}_{'fp64' if dom['fp64'] else 'fp32'}"
+            if tj.get("workload") == args.workload and key in tj.get("kernels", {}):
+                traffic = tj["kernels"][key]
+        except Exception:
+            traffic = None
+
+    # end to end through the public host-buffer call: H2D of D, the build, D2H of J and K
+    e2e_t = []
+    for _ in range(max(2, min(args.steps, 5))):
+        t0 = time.perf_counter()
+        g.jk(D, prec=args.prec, schwarz_tau=SCHWARZ_TAU, fp64_tau=args.fp64_tau)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_t)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, threads, dt = _oracle_rate(mol, bpath, args.cpu_elements)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_elements} sampled J/K elements of the same workload, each by its defining "
+                         f"sum over all (l, s): 2 n^2 integral evaluations per element ({dt:.1f} s of CPU work)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.prec != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": w["desc"], "nbf": n, "precision": args.prec,
+                   "schwarz_tau": SCHWARZ_TAU, "fp64_tau": args.fp64_tau if args.fp64_tau else 3e-2,
+                   "density": "converged RHF density of the workload", "l2": "flushed (512 MiB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "shell_quartets_per_step": info["shell_quartets"], "function_quartets_per_step": fnq,
+        "shell_quartets_fp64_per_step": info["shell_quartets_fp64"],
+        "shell_quartets_per_s": world * info["shell_quartets"] * args.steps / (max_ms * 1e-3),
+        "energy_error_vs_fp64_Ha": dE,
+        "fp64_path": {"value": fp64_rate, "unit": UNIT, "ms_per_step": ms64 / fp64_steps,
+                      "speedup_of_reduced_precision": fp64_rate and value / world / fp64_rate},
+        "gpu_launches": int(info["kernel_launches"]) * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": f"k_jk_{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']} ({'FP64' if dom['fp64'] else 'FP32'})",
+                     "kernel_ms": dom["ms"], "kernel_share": dom["ms"] / tot_ms,
+                     "peak_source": f"measured FMA-chain peak of this GPU ({'FP64' if dom['fp64'] else 'FP32'})",
+                     "whole_build": {"achieved": tot_flops / (tot_ms * 1e-3) / 1e12, "ms": tot_ms}},
+        "peaks_measured_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
+        "e2e": {"value": fnq / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8},
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if args.breakdown:
+        line["kernels"] = [{k: p[k] for k in ("la", "lb", "lc", "ld", "fp64", "shell_quartets", "primitive_quartets",
+                                             "flops", "ms")} for p in prof]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier(device_ids=[local_rank])
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water8", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--fp64-tau", dest="fp64_tau", type=float, default=0.0)
+    ap.add_argument("--cpu-elements", dest="cpu_elements", type=int, default=320)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--breakdown", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

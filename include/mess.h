@@ -1,0 +1,180 @@
+/*
+ * mess.h - C ABI of the GB300 Gaussian-basis Hartree-Fock hot path.
+ *
+ * The calls follow the problem statement of MESS (Helal & Fitzgibbon, arXiv 2406.03121):
+ *   Structure(Z, positions) -> basisset(mol, name) -> one-electron integrals, the Coulomb / exchange
+ *   contraction of the repulsion integrals with a density, the energy functional H(P) +
+ *   nuclear_energy, and the self-consistent-field solution of the Roothaan equation.
+ *
+ * Conventions (all calls):
+ *   - Units: bohr and hartree.  Atomic numbers are ints; coordinates natom x 3 row-major doubles.
+ *   - Basis functions are contracted Cartesian Gaussians (paper Sec. 3, Eq. 1): per atom in input
+ *     order, per shell in basis-file order, per Cartesian component in the order
+ *     x^l y^m z^n with l descending then m descending (p: x y z; d: xx xy xz yy yz zz).  Every
+ *     function is normalised on its own (S_mm = 1).  n = mess_basis_nbf().
+ *   - Matrices are n x n row-major doubles.  D is the total closed-shell density 2 C_occ C_occ^T.
+ *   - J_mn = sum_ls (mn|ls) D_ls and K_mn = sum_ls (ml|ns) D_ls (Hartree-Fock exchange, the
+ *     paper's xc_method="hfx"); the Fock matrix is F = H + J - K/2 and the electronic energy
+ *     E_elec = 1/2 sum D (H + F) (the paper's H(P), Sec. 5.1).
+ *   - Ownership: every output buffer is caller-owned.  mess_basis is library-owned (create/destroy).
+ *     Host-buffer calls copy through internal device buffers and synchronise before returning.
+ *   - Errors: every call returns a mess_status; no exception crosses the ABI.  mess_last_error()
+ *     returns a message for the calling thread's most recent failure.
+ *   - Threads: calls on distinct bases are independent.  A mess_basis may be shared by calls that do
+ *     not overlap in time on the host (it caches screening bins); device-pointer calls on the same
+ *     basis may overlap on the GPU.
+ */
+#ifndef MESS_H
+#define MESS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mess_basis mess_basis; /* opaque, library-owned */
+
+typedef enum {
+    MESS_OK = 0,
+    MESS_EINVAL = -1,     /* bad argument (null pointer, size, unknown element, malformed file) */
+    MESS_ENOMEM = -2,     /* device or host allocation failed */
+    MESS_ECUDA = -3,      /* CUDA runtime error (message in mess_last_error) */
+    MESS_ENOCONV = -4,    /* SCF did not converge within max_iter (result holds the last iterate) */
+    MESS_ENUMERIC = -5,   /* non-finite value detected */
+    MESS_ETIMEOUT = -6,   /* a bounded device wait gave up */
+    MESS_ENOTIMPL = -7    /* feature not available */
+} mess_status;
+
+typedef enum {
+    MESS_FP64 = 0,  /* all recursion arithmetic in FP64 */
+    MESS_MIXED = 1, /* FP32 recursion and FP32 per-quartet digestion; the shell quartets with
+                       Q_ab Q_cd >= fp64_tau (the largest integrals) in FP64; FP64 J/K accumulation */
+    MESS_FP32 = 2   /* FP32 recursion for every quartet; FP64 J/K accumulation */
+} mess_precision;
+
+/* Default MESS_MIXED split: quartets with Q_ab Q_cd >= 3e-2 run in FP64. */
+#define MESS_DEFAULT_FP64_TAU 3e-2
+
+/* J/K build options.  Zero-initialised opts mean FP64, no screening, default stream. */
+typedef struct {
+    mess_precision prec;
+    double schwarz_tau; /* drop shell quartets with Q_ab Q_cd < schwarz_tau (0: keep all) */
+    double fp64_tau;    /* MESS_MIXED: quartets with Q_ab Q_cd >= fp64_tau run in FP64;
+                           0 selects MESS_DEFAULT_FP64_TAU, < 0 runs every quartet in FP32 */
+    int boys_fp64;      /* MESS_MIXED / MESS_FP32: 1 evaluates the Boys function of the FP32 quartets
+                           in FP64 for T < 36 (Taylor grid + downward recursion), 0 in FP32 */
+    void* cuda_stream;  /* cudaStream_t for the device-pointer calls (NULL: default stream) */
+} mess_jk_opts;
+
+/* Work done by one J/K build (after screening). */
+typedef struct {
+    long long shell_quartets;        /* unique shell quartets evaluated */
+    long long function_quartets;     /* unique Cartesian function quartets evaluated */
+    long long shell_quartets_fp64;   /* of which evaluated in FP64 */
+    long long primitive_quartets;    /* primitive quartets evaluated */
+    long long kernel_launches;       /* kernels launched by the call */
+} mess_jk_info;
+
+typedef enum { MESS_GUESS_CORE = 0, MESS_GUESS_SAD = 1, MESS_GUESS_MLP = 2 } mess_guess;
+
+typedef struct {
+    mess_precision prec;  /* precision of the J/K builds */
+    int guess;            /* mess_guess */
+    int max_iter;         /* default 100 when <= 0 */
+    double conv_E;        /* |dE| threshold, default 1e-10 when <= 0 */
+    double conv_comm;     /* max|FDS - SDF| threshold, default 1e-8 when <= 0 */
+    int diis_n;           /* DIIS subspace size, default 8 when <= 0 */
+    double schwarz_tau;   /* screening threshold for the J/K builds */
+    double fp64_tau;      /* MESS_MIXED split, see mess_jk_opts */
+    int boys_fp64;        /* see mess_jk_opts */
+    const char* mlp_weights; /* MESS_GUESS_MLP: weight file (unused otherwise) */
+    void* cuda_stream;
+} mess_scf_opts;
+
+typedef struct {
+    double E_total, E_elec, E_nuc;
+    int iterations, converged;
+} mess_scf_result;
+
+/* Build the contracted Cartesian basis of a structure (paper Sec. 3 LCAO basis; Sec. 5.1 basisset)
+ * from a basis data file: "element <sym>" lines followed by shells "<S|P|D|SP> <nprim>" and nprim
+ * lines "exponent coefficient(s)".  Computes on the GPU the primitive-pair tables (Gaussian product
+ * theorem) and the Schwarz factors Q_ab = sqrt(max |(mn|mn)|) of every shell pair.
+ * Z: natom ints; xyz_bohr: natom*3 doubles.  *out receives a new basis (free with mess_basis_destroy).
+ * Errors: MESS_EINVAL (unknown element, unreadable or malformed file, natom <= 0), MESS_ENOMEM,
+ * MESS_ECUDA. */
+mess_status mess_basis_create(int natom, const int* Z, const double* xyz_bohr, const char* basis_file,
+                              mess_basis** out);
+int mess_basis_nbf(const mess_basis* b);      /* number of basis functions n (-1 if b is NULL) */
+int mess_basis_nshell(const mess_basis* b);   /* number of shells */
+int mess_basis_nelectron(const mess_basis* b);/* sum of Z */
+void mess_basis_destroy(mess_basis* b);       /* NULL is accepted */
+
+/* Overlap S_mn = <phi_m|phi_n> (paper Eq. 3), kinetic T_mn = <phi_m|-1/2 nabla^2|phi_n>, nuclear
+ * attraction V_mn = -sum_C Z_C <phi_m|1/|r-C||phi_n> (the "closed-form expressions for all the
+ * relevant integrals", Sec. 3).  Output: caller-owned host n*n doubles. */
+mess_status mess_overlap(const mess_basis* b, double* S);
+mess_status mess_kinetic(const mess_basis* b, double* T);
+mess_status mess_nuclear(const mess_basis* b, double* V);
+/* The same three on device pointers (each n*n doubles, any may be NULL), on cuda_stream. */
+mess_status mess_one_e_device(const mess_basis* b, double* dS, double* dT, double* dV, void* cuda_stream);
+
+/* sum_{A<B} Z_A Z_B / R_AB (the paper's nuclear_energy, Sec. 5.1).  NaN if b is NULL. */
+double mess_nuclear_repulsion(const mess_basis* b);
+
+/* Integral-direct Coulomb and exchange matrices of a symmetric density (Sec. 3 / 5.1 "hfx"):
+ * J_mn = sum_ls (mn|ls) D_ls, K_mn = sum_ls (ml|ns) D_ls, over the unique shell quartets that pass
+ * Schwarz screening, with the 8-fold permutational symmetry.  D, J, K: host n*n doubles
+ * (caller-owned).  opts may be NULL (FP64, no screening).  info may be NULL.
+ * Errors: MESS_EINVAL, MESS_ENOMEM, MESS_ECUDA. */
+mess_status mess_jk_build(const mess_basis* b, const double* D, double* J, double* K,
+                          const mess_jk_opts* opts, mess_jk_info* info);
+/* Same on caller-owned device buffers (n*n doubles each), enqueued on opts->cuda_stream; returns
+ * after enqueueing (no synchronisation).  dD must not alias dJ or dK. */
+mess_status mess_jk_build_device(const mess_basis* b, const double* dD, double* dJ, double* dK,
+                                 const mess_jk_opts* opts, mess_jk_info* info);
+
+/* Every repulsion integral (mn|ls) in FP64 as a dense n^4 host tensor (index ((m*n+n')*n+l)*n+s).
+ * For small bases only (n <= 64).  Errors: MESS_EINVAL (n > 64), MESS_ENOMEM, MESS_ECUDA. */
+mess_status mess_eri_tensor(const mess_basis* b, double* G);
+
+/* Schwarz factor of every shell pair as an nshell x nshell host matrix (symmetric). */
+mess_status mess_schwarz(const mess_basis* b, double* Q);
+
+/* Closed-shell Roothaan SCF (paper Eq. 2, Sec. 3): Loewdin orthogonalisation, core-Hamiltonian
+ * guess, Pulay DIIS on FDS - SDF, converged when |dE| < conv_E and max|FDS - SDF| < conv_comm.
+ * D_out (nullable): host n*n final density.  Errors: MESS_ENOCONV (res holds the last iterate),
+ * MESS_EINVAL (odd electron count), MESS_ENOMEM, MESS_ECUDA, MESS_ENUMERIC. */
+mess_status mess_scf(const mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* D_out);
+
+/* Batched SCF over many molecules (the paper's vmap over conformers, Sec. 5.2).  res: nmol entries. */
+mess_status mess_scf_batch(int nmol, mess_basis* const* bases, const mess_scf_opts* opts, mess_scf_result* res);
+
+/* One kernel launch of a profiled J/K build. */
+typedef struct {
+    int qclass;                  /* shell-quartet class index (la lb | lc ld), see mess_jk_class_info */
+    int la, lb, lc, ld;
+    int fp64;                    /* 1: FP64 kernel, 0: FP32 kernel */
+    long long shell_quartets, primitive_quartets, function_quartets;
+    double flops;                /* algorithmic flops of the launch (op counts of the recursion, Boys,
+                                    contraction, HRR and digestion; an FMA counts as 2) */
+    double ms;                   /* launch duration, CUDA events on opts->cuda_stream */
+} mess_jk_part;
+
+/* Diagnostic: the J/K build of mess_jk_build_device with a CUDA event pair around every kernel
+ * launch; synchronises opts->cuda_stream and fills parts[0..*nparts) (at most max_parts).
+ * Errors: as mess_jk_build_device, MESS_EINVAL if max_parts is too small. */
+mess_status mess_jk_profile(const mess_basis* b, const double* dD, double* dJ, double* dK,
+                            const mess_jk_opts* opts, mess_jk_part* parts, int max_parts, int* nparts);
+
+/* Diagnostic (not part of the paper's method): measured CUDA-core FMA throughput of this GPU in
+ * TFLOP/s (2 flops per FMA), FP32 and FP64, from independent FMA chains timed with CUDA events on
+ * cuda_stream.  Used as the roofline denominator of the ALU-bound integral kernels. */
+mess_status mess_fma_peak(double* fp32_tflops, double* fp64_tflops, void* cuda_stream);
+
+/* Message for the calling thread's most recent failure ("" if none).  Valid until the next call. */
+const char* mess_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MESS_H */

@@ -1,0 +1,295 @@
+"""Python binding of ``libmess.so`` (include/mess.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays / torch tensors to
+pointers and status codes to exceptions.  There is no CPU fallback: importing the package fails
+loudly when the compiled library is missing (build it with ``paper_2406_03121_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmess.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libmess.so not built ({LIB_PATH}); run paper_2406_03121_gb300.build.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MESS_OK, MESS_EINVAL, MESS_ENOMEM, MESS_ECUDA = 0, -1, -2, -3
+MESS_ENOCONV, MESS_ENUMERIC, MESS_ETIMEOUT, MESS_ENOTIMPL = -4, -5, -6, -7
+MESS_FP64, MESS_MIXED, MESS_FP32 = 0, 1, 2
+MESS_GUESS_CORE, MESS_GUESS_SAD, MESS_GUESS_MLP = 0, 1, 2
+PRECISION = {"fp64": MESS_FP64, "mixed": MESS_MIXED, "fp32": MESS_FP32}
+
+EXPORTED = [
+    "mess_basis_create", "mess_basis_nbf", "mess_basis_nshell", "mess_basis_nelectron",
+    "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
+    "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_eri_tensor",
+    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_fma_peak", "mess_last_error",
+]
+
+
+class mess_jk_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("schwarz_tau", ctypes.c_double), ("fp64_tau", ctypes.c_double),
+                ("boys_fp64", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class mess_jk_info(ctypes.Structure):
+    _fields_ = [("shell_quartets", ctypes.c_longlong), ("function_quartets", ctypes.c_longlong),
+                ("shell_quartets_fp64", ctypes.c_longlong), ("primitive_quartets", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class mess_jk_part(ctypes.Structure):
+    _fields_ = [("qclass", ctypes.c_int), ("la", ctypes.c_int), ("lb", ctypes.c_int), ("lc", ctypes.c_int),
+                ("ld", ctypes.c_int), ("fp64", ctypes.c_int), ("shell_quartets", ctypes.c_longlong),
+                ("primitive_quartets", ctypes.c_longlong), ("function_quartets", ctypes.c_longlong),
+                ("flops", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class mess_scf_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("guess", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("conv_E", ctypes.c_double), ("conv_comm", ctypes.c_double), ("diis_n", ctypes.c_int),
+                ("schwarz_tau", ctypes.c_double), ("fp64_tau", ctypes.c_double), ("boys_fp64", ctypes.c_int),
+                ("mlp_weights", ctypes.c_char_p), ("cuda_stream", ctypes.c_void_p)]
+
+
+class mess_scf_result(ctypes.Structure):
+    _fields_ = [("E_total", ctypes.c_double), ("E_elec", ctypes.c_double), ("E_nuc", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("converged", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+mess_basis_create = _sig("mess_basis_create", ctypes.c_int,
+                         [ctypes.c_int, _IP, _DP, ctypes.c_char_p, ctypes.POINTER(_P)])
+mess_basis_nbf = _sig("mess_basis_nbf", ctypes.c_int, [_P])
+mess_basis_nshell = _sig("mess_basis_nshell", ctypes.c_int, [_P])
+mess_basis_nelectron = _sig("mess_basis_nelectron", ctypes.c_int, [_P])
+mess_basis_destroy = _sig("mess_basis_destroy", None, [_P])
+mess_overlap = _sig("mess_overlap", ctypes.c_int, [_P, _DP])
+mess_kinetic = _sig("mess_kinetic", ctypes.c_int, [_P, _DP])
+mess_nuclear = _sig("mess_nuclear", ctypes.c_int, [_P, _DP])
+mess_one_e_device = _sig("mess_one_e_device", ctypes.c_int, [_P, _P, _P, _P, _P])
+mess_nuclear_repulsion = _sig("mess_nuclear_repulsion", ctypes.c_double, [_P])
+mess_jk_build = _sig("mess_jk_build", ctypes.c_int,
+                     [_P, _DP, _DP, _DP, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_info)])
+mess_jk_build_device = _sig("mess_jk_build_device", ctypes.c_int,
+                            [_P, _P, _P, _P, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_info)])
+mess_eri_tensor = _sig("mess_eri_tensor", ctypes.c_int, [_P, _DP])
+mess_schwarz = _sig("mess_schwarz", ctypes.c_int, [_P, _DP])
+mess_scf = _sig("mess_scf", ctypes.c_int,
+                [_P, ctypes.POINTER(mess_scf_opts), ctypes.POINTER(mess_scf_result), _DP])
+mess_scf_batch = _sig("mess_scf_batch", ctypes.c_int,
+                      [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(mess_scf_opts),
+                       ctypes.POINTER(mess_scf_result)])
+mess_jk_profile = _sig("mess_jk_profile", ctypes.c_int,
+                       [_P, _P, _P, _P, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_part), ctypes.c_int,
+                        ctypes.POINTER(ctypes.c_int)])
+mess_fma_peak = _sig("mess_fma_peak", ctypes.c_int, [_DP, _DP, _P])
+mess_last_error = _sig("mess_last_error", ctypes.c_char_p, [])
+
+
+class MessError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = mess_last_error().decode(errors="replace")
+        super().__init__(f"{where}: status {status}: {msg}")
+
+
+def _check(st, where):
+    if st != MESS_OK:
+        raise MessError(st, where)
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+def _tptr(t):
+    """device pointer of a contiguous float64 CUDA tensor"""
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def jk_opts(prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False) -> mess_jk_opts:
+    p = PRECISION[prec] if isinstance(prec, str) else int(prec)
+    return mess_jk_opts(p, float(schwarz_tau), float(fp64_tau), int(bool(boys_fp64)), _stream_handle(stream))
+
+
+class Basis:
+    """A contracted Cartesian Gaussian basis of one structure (owns a ``mess_basis``)."""
+
+    def __init__(self, Z, xyz_bohr, basis_file: str):
+        Z = np.ascontiguousarray(np.asarray(Z, dtype=np.int32).ravel())
+        xyz = np.ascontiguousarray(np.asarray(xyz_bohr, dtype=np.float64).reshape(-1, 3))
+        if xyz.shape[0] != Z.shape[0]:
+            raise ValueError("Z and xyz disagree on the atom count")
+        h = _P()
+        _check(mess_basis_create(int(Z.shape[0]), Z.ctypes.data_as(_IP), _dptr(xyz),
+                                 os.fsencode(basis_file), ctypes.byref(h)), "mess_basis_create")
+        self._h = h
+        self.Z, self.xyz, self.basis_file = Z, xyz, basis_file
+
+    @classmethod
+    def from_molecule(cls, mol, basis_file: str):
+        return cls(mol.Z, mol.xyz, basis_file)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            mess_basis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nbf(self) -> int:
+        return int(mess_basis_nbf(self._h))
+
+    @property
+    def nshell(self) -> int:
+        return int(mess_basis_nshell(self._h))
+
+    @property
+    def nelectron(self) -> int:
+        return int(mess_basis_nelectron(self._h))
+
+    def _mat(self, fn, name):
+        out = np.zeros((self.nbf, self.nbf))
+        _check(fn(self._h, _dptr(out)), name)
+        return out
+
+    def overlap(self):
+        return self._mat(mess_overlap, "mess_overlap")
+
+    def kinetic(self):
+        return self._mat(mess_kinetic, "mess_kinetic")
+
+    def nuclear(self):
+        return self._mat(mess_nuclear, "mess_nuclear")
+
+    def one_e_device(self, S=None, T=None, V=None, stream=None):
+        ptr = lambda t: None if t is None else _tptr(t)  # noqa: E731
+        _check(mess_one_e_device(self._h, ptr(S), ptr(T), ptr(V), _stream_handle(stream)), "mess_one_e_device")
+
+    def nuclear_repulsion(self) -> float:
+        return float(mess_nuclear_repulsion(self._h))
+
+    def schwarz(self):
+        out = np.zeros((self.nshell, self.nshell))
+        _check(mess_schwarz(self._h, _dptr(out)), "mess_schwarz")
+        return out
+
+    def eri_tensor(self):
+        n = self.nbf
+        out = np.zeros((n, n, n, n))
+        _check(mess_eri_tensor(self._h, _dptr(out)), "mess_eri_tensor")
+        return out
+
+    def jk(self, D, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, boys_fp64=False):
+        """J, K of a host density (numpy); returns (J, K, info dict)."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        J, K = np.zeros_like(D), np.zeros_like(D)
+        info = mess_jk_info()
+        o = jk_opts(prec, schwarz_tau, fp64_tau, None, boys_fp64)
+        _check(mess_jk_build(self._h, _dptr(D), _dptr(J), _dptr(K), ctypes.byref(o), ctypes.byref(info)),
+               "mess_jk_build")
+        return J, K, info.as_dict()
+
+    def jk_device(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False):
+        """J, K of a device density (torch float64 CUDA tensors, caller-owned); enqueued on stream."""
+        info = mess_jk_info()
+        o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64)
+        _check(mess_jk_build_device(self._h, _tptr(D), _tptr(J), _tptr(K), ctypes.byref(o), ctypes.byref(info)),
+               "mess_jk_build_device")
+        return info.as_dict()
+
+    def jk_profile(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False):
+        """Per-launch timings (CUDA events) and algorithmic flops of one device J/K build."""
+        parts = (mess_jk_part * 128)()
+        n = ctypes.c_int()
+        o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64)
+        _check(mess_jk_profile(self._h, _tptr(D), _tptr(J), _tptr(K), ctypes.byref(o), parts, 128, ctypes.byref(n)),
+               "mess_jk_profile")
+        return [parts[i].as_dict() for i in range(n.value)]
+
+    def scf(self, prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8, diis_n=8,
+            schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, want_density=True):
+        o = scf_opts(prec, guess, max_iter, conv_E, conv_comm, diis_n, schwarz_tau, fp64_tau, mlp_weights, stream)
+        res = mess_scf_result()
+        D = np.zeros((self.nbf, self.nbf)) if want_density else None
+        st = mess_scf(self._h, ctypes.byref(o), ctypes.byref(res), _dptr(D) if D is not None else None)
+        if st not in (MESS_OK, MESS_ENOCONV):
+            _check(st, "mess_scf")
+        out = res.as_dict()
+        out["status"] = st
+        out["D"] = D
+        return out
+
+
+def fma_peak(stream=None):
+    """Measured FP32 and FP64 CUDA-core FMA throughput in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(mess_fma_peak(ctypes.byref(a), ctypes.byref(b), _stream_handle(stream)), "mess_fma_peak")
+    return a.value, b.value
+
+
+def scf_opts(prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8, diis_n=8,
+             schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, boys_fp64=False) -> mess_scf_opts:
+    p = PRECISION[prec] if isinstance(prec, str) else int(prec)
+    w = os.fsencode(mlp_weights) if mlp_weights else None
+    return mess_scf_opts(p, int(guess), int(max_iter), float(conv_E), float(conv_comm), int(diis_n),
+                         float(schwarz_tau), float(fp64_tau), int(bool(boys_fp64)), w, _stream_handle(stream))
+
+
+def scf_batch(bases, prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8,
+              diis_n=8, schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None):
+    """Batched SCF over many bases; returns a list of result dicts and the call's status."""
+    n = len(bases)
+    arr = (_P * n)(*[b.handle for b in bases])
+    res = (mess_scf_result * n)()
+    o = scf_opts(prec, guess, max_iter, conv_E, conv_comm, diis_n, schwarz_tau, fp64_tau, mlp_weights, stream)
+    st = mess_scf_batch(n, arr, ctypes.byref(o), res)
+    if st not in (MESS_OK, MESS_ENOCONV):
+        _check(st, "mess_scf_batch")
+    return [r.as_dict() for r in res], st

@@ -1,0 +1,392 @@
+// Device-side building blocks shared by the generated per-class ERI code and the kernels:
+// primitive-pair tables, the Boys function F_m(T), and J/K accumulation helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mess_device.h"
+
+// ------------------------------------------------------------------------------------------
+// Primitive-pair record (Gaussian product theorem): for primitives alpha on A, beta on B,
+//   zeta = alpha + beta,  P = (alpha A + beta B)/zeta,  PA = P - A,
+//   K = sqrt(2) pi^{5/4} c_a c_b exp(-alpha beta/zeta |AB|^2) / zeta   (so that K_ab K_cd / sqrt(zeta+eta)
+//       is the 2 pi^{5/2}/(zeta eta sqrt(zeta+eta)) prefactor of [00|00]^(m)),
+//   oo2z = 1/(2 zeta).
+// ------------------------------------------------------------------------------------------
+template <typename R> struct PrimPair { R zeta, Px, Py, Pz, PAx, PAy, PAz, K, oo2z; };
+
+template <typename R> struct PairTable {
+    const PrimPairRec<R>* __restrict__ pp;   // [npp]
+    const int* __restrict__ pp_off;          // [npair]
+    const int* __restrict__ pp_n;            // [npair]
+    const double* __restrict__ AB;           // [npair][3]  A - B
+    const int* __restrict__ fa;              // [npair] first function of A
+    const int* __restrict__ fb;              // [npair] first function of B
+    const int* __restrict__ same;            // [npair] 1 if A == B (same shell)
+    const double* __restrict__ C;            // [npair][3] centre of the pair's first shell A
+    const double* __restrict__ boys64;       // Boys grid, FP64
+    const float* __restrict__ boys32;        // Boys grid, FP32
+
+    __device__ __forceinline__ PrimPair<R> load(int i) const
+    {
+        const PrimPairRec<R>& r = pp[i];
+        PrimPair<R> o;
+        o.zeta = r.v[0]; o.Px = r.v[1]; o.Py = r.v[2]; o.Pz = r.v[3];
+        o.PAx = r.v[4]; o.PAy = r.v[5]; o.PAz = r.v[6]; o.K = r.v[7];
+        o.oo2z = r.v[8];
+        return o;
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+// Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt, m = 0..L.
+// Grid tables tab[k][n] = F_n(k dT) for n = 0..MESS_BOYS_NF-1 and tab[k][MESS_BOYS_NF] = exp(-k dT).
+//   small T: Taylor expansion about the nearest grid point, F_n(T) = sum_j F_{n+j}(T_k) (-x)^j / j!,
+//            x = T - T_k (|x| <= dT/2), for the highest order L, then the stable downward recursion
+//            F_{m-1} = (2 T F_m + exp(-T)) / (2m - 1);
+//   large T: F_0 = (1/2) sqrt(pi/T) (erf(sqrt T) = 1 to working precision there) and the upward
+//            recursion F_{m+1} = ((2m+1) F_m - exp(-T)) / (2T), stable for large T.
+// BMODE 0: everything in FP64.  BMODE 1: FP64 for T < MESS_BOYS_TMAX64 (small-T Taylor + downward
+// recursion), FP32 asymptote above it.  BMODE 2: everything in FP32.
+// ------------------------------------------------------------------------------------------
+template <int L> __device__ __forceinline__ void boys_small_f64(double T, double* F, const double* __restrict__ c_boys64)
+{
+    const int k = __double2int_rn(T * MESS_BOYS_INV_DT);
+    const double x = (double)k * MESS_BOYS_DT - T;      // = -(T - T_k)
+    const double* row = c_boys64 + (size_t)k * MESS_BOYS_NCOL;
+    if (L == 0) {
+        double s = __ldg(row + 7);
+#pragma unroll
+        for (int j = 7; j >= 1; --j) s = __ldg(row + j - 1) + s * x * (1.0 / j);
+        F[0] = s;
+        return;
+    }
+    double s = __ldg(row + L + 7);
+#pragma unroll
+    for (int j = 7; j >= 1; --j) s = __ldg(row + L + j - 1) + s * x * (1.0 / j);
+    F[L] = s;
+    // exp(-T) = exp(-T_k) * exp(x), exp(x) by its Taylor series (|x| <= 0.05)
+    double ex = 1.0 + x * (1.0 + x * (1.0 / 2 + x * (1.0 / 6 + x * (1.0 / 24 + x * (1.0 / 120
+                + x * (1.0 / 720 + x * (1.0 / 5040 + x * (1.0 / 40320))))))));
+    const double e = __ldg(row + MESS_BOYS_NF) * ex;
+    const double t2 = 2.0 * T;
+#pragma unroll
+    for (int m = L; m >= 1; --m) F[m - 1] = (t2 * F[m] + e) * (1.0 / (2 * m - 1));
+}
+
+template <int L> __device__ __forceinline__ void boys_large_f64(double T, double* F)
+{
+    const double rt = rsqrt(T);
+    F[0] = 0.886226925452758014 * rt;   // sqrt(pi)/2 / sqrt(T)
+    if (L > 0) {
+        const double e = exp(-T);
+        const double h = 0.5 * rt * rt;
+#pragma unroll
+        for (int m = 0; m < L; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * h;
+    }
+}
+
+template <int L> __device__ __forceinline__ void boys_small_f32(float T, float* F, const float* __restrict__ c_boys32)
+{
+    const int k = __float2int_rn(T * (float)MESS_BOYS_INV_DT);
+    const float x = (float)k * (float)MESS_BOYS_DT - T;
+    const float* row = c_boys32 + (size_t)k * MESS_BOYS_NCOL;
+    if (L == 0) {
+        float s = __ldg(row + 4);
+#pragma unroll
+        for (int j = 4; j >= 1; --j) s = __ldg(row + j - 1) + s * x * (1.0f / j);
+        F[0] = s;
+        return;
+    }
+    float s = __ldg(row + L + 4);
+#pragma unroll
+    for (int j = 4; j >= 1; --j) s = __ldg(row + L + j - 1) + s * x * (1.0f / j);
+    F[L] = s;
+    const float ex = 1.0f + x * (1.0f + x * (0.5f + x * (1.0f / 6 + x * (1.0f / 24 + x * (1.0f / 120)))));
+    const float e = __ldg(row + MESS_BOYS_NF) * ex;
+    const float t2 = 2.0f * T;
+#pragma unroll
+    for (int m = L; m >= 1; --m) F[m - 1] = (t2 * F[m] + e) * (1.0f / (2 * m - 1));
+}
+
+template <int L> __device__ __forceinline__ void boys_large_f32(float T, float* F)
+{
+    const float rt = rsqrtf(T);
+    F[0] = 0.886226925f * rt;
+    if (L > 0) {
+        const float e = __expf(-T);
+        const float h = 0.5f * rt * rt;
+#pragma unroll
+        for (int m = 0; m < L; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * h;
+    }
+}
+
+template <typename R, int L, int BMODE>
+__device__ __forceinline__ void boys_eval(R T, R* F, const double* t64, const float* t32);
+
+template <> __device__ __forceinline__ void boys_eval<double, 0, 0>(double T, double* F, const double* t64, const float*)
+{ if (T < MESS_BOYS_TMAX64) boys_small_f64<0>(T, F, t64); else boys_large_f64<0>(T, F); }
+
+#define MESS_BOYS_SPECIALISE(LL)                                                                  \
+    template <> __device__ __forceinline__ void boys_eval<double, LL, 0>(double T, double* F,     \
+                                                                        const double* t64, const float*) \
+    { if (T < MESS_BOYS_TMAX64) boys_small_f64<LL>(T, F, t64); else boys_large_f64<LL>(T, F); }   \
+    template <> __device__ __forceinline__ void boys_eval<float, LL, 1>(float T, float* F,        \
+                                                                       const double* t64, const float*) \
+    {                                                                                             \
+        if (T < (float)MESS_BOYS_TMAX64) {                                                        \
+            double Fd[LL + 1];                                                                    \
+            boys_small_f64<LL>((double)T, Fd, t64);                                               \
+            _Pragma("unroll") for (int m = 0; m <= LL; ++m) F[m] = (float)Fd[m];                  \
+        } else {                                                                                  \
+            boys_large_f32<LL>(T, F);                                                             \
+        }                                                                                         \
+    }                                                                                             \
+    template <> __device__ __forceinline__ void boys_eval<float, LL, 2>(float T, float* F,        \
+                                                                       const double*, const float* t32) \
+    { if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<LL>(T, F, t32); else boys_large_f32<LL>(T, F); }
+
+MESS_BOYS_SPECIALISE(1)
+MESS_BOYS_SPECIALISE(2)
+MESS_BOYS_SPECIALISE(3)
+MESS_BOYS_SPECIALISE(4)
+MESS_BOYS_SPECIALISE(5)
+MESS_BOYS_SPECIALISE(6)
+MESS_BOYS_SPECIALISE(7)
+MESS_BOYS_SPECIALISE(8)
+
+template <> __device__ __forceinline__ void boys_eval<float, 0, 1>(float T, float* F, const double* t64, const float*)
+{
+    if (T < (float)MESS_BOYS_TMAX64) { double Fd[1]; boys_small_f64<0>((double)T, Fd, t64); F[0] = (float)Fd[0]; }
+    else boys_large_f32<0>(T, F);
+}
+template <> __device__ __forceinline__ void boys_eval<float, 0, 2>(float T, float* F, const double*, const float* t32)
+{ if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<0>(T, F, t32); else boys_large_f32<0>(T, F); }
+
+__device__ __forceinline__ double prefactor_sqrt(double rz) { return sqrt(rz); }
+__device__ __forceinline__ float prefactor_sqrt(float rz) { return sqrtf(rz); }
+
+// ------------------------------------------------------------------------------------------
+// J/K accumulation.  For a unique shell quartet (ab|cd) (pair ab >= pair cd, a >= b, c >= d by
+// the canonical pair order) with degeneracy weight s = (1/2)^{[a=b] + [c=d] + [ab=cd]}:
+//   Jacc_ab += s sum_cd I D_cd,   Jacc_cd += s sum_ab I D_ab,
+//   Kacc_ac += s sum_bd I D_bd,   Kacc_ad += s sum_bc I D_bc,
+//   Kacc_bc += s sum_ad I D_ad,   Kacc_bd += s sum_ac I D_ac,
+// and afterwards J = 2 (Jacc + Jacc^T), K = Kacc + Kacc^T.  This visits each of the 8 index
+// permutations of every function quartet exactly once for a symmetric D.
+// ------------------------------------------------------------------------------------------
+struct DigestCtx {
+    const double* __restrict__ D;
+    double* __restrict__ J;
+    double* __restrict__ K;
+    int n;
+    int fa, fb, fc, fd;
+    bool warp_reduce_ab;   // all 32 lanes share the bra pair: reduce J_ab across the warp first
+};
+
+template <typename R> __device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R>
+__device__ __forceinline__ void jk_add(double* __restrict__ M, size_t idx, R v, bool warp_reduce)
+{
+    if (warp_reduce) {
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) atomicAdd(M + idx, (double)v);
+    } else {
+        if (v != R(0)) atomicAdd(M + idx, (double)v);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Work decomposition of one class bin: bra pairs i (sorted by Q descending), each with a
+// contiguous ket range [kbeg[i], kbeg[i] + offs[i+1] - offs[i]) of the ket list.  A flat quartet
+// index q maps to (i, j) by a binary search over offs.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int find_bra(const long long* __restrict__ offs, int nbra, long long q)
+{
+    int lo = 0, hi = nbra - 1;   // largest i with offs[i] <= q
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(offs + mid) <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool warp_uniform_int(int v)
+{
+    const int v0 = __shfl_sync(0xffffffffu, v, 0);
+    return __all_sync(0xffffffffu, v == v0);
+}
+
+#define MESS_THREADS 128
+
+// JK kernel of one class: one thread per shell quartet of the bin.
+#define MESS_DEFINE_CLASS_KERNELS(TAG, NA, NB, NC, ND)                                             \
+    template <typename R, int BMODE>                                                                \
+    __global__ void __launch_bounds__(MESS_THREADS)                                                 \
+    k_jk_##TAG(const BinLaunch b, const PairTable<R> P, const double* __restrict__ D,               \
+               double* __restrict__ J, double* __restrict__ K, int n)                               \
+    {                                                                                               \
+        const long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;                     \
+        const bool valid = q0 < b.total;                                                            \
+        const long long q = valid ? q0 : b.total - 1;                                               \
+        const int i = find_bra(b.offs, b.nbra, q);                                                  \
+        const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));                            \
+        const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);                                     \
+        R I[(NA) * (NB) * (NC) * (ND)];                                                             \
+        eri_##TAG<R, BMODE>(P, bp, kp, I);                                                          \
+        DigestCtx c;                                                                                \
+        c.D = D; c.J = J; c.K = K; c.n = n;                                                         \
+        c.fa = __ldg(P.fa + bp); c.fb = __ldg(P.fb + bp);                                           \
+        c.fc = __ldg(P.fa + kp); c.fd = __ldg(P.fb + kp);                                           \
+        R s = valid ? R(1) : R(0);                                                                  \
+        if (__ldg(P.same + bp)) s *= R(0.5);                                                        \
+        if (__ldg(P.same + kp)) s *= R(0.5);                                                        \
+        if (bp == kp) s *= R(0.5);                                                                  \
+        c.warp_reduce_ab = warp_uniform_int(bp);                                                    \
+        digest_##TAG<R>(I, c, s);                                                                   \
+    }                                                                                               \
+    /* every integral of the bin written to a dense n^4 tensor, all 8 index permutations */         \
+    __global__ void __launch_bounds__(MESS_THREADS)                                                 \
+    k_store_##TAG(const BinLaunch b, const PairTable<double> P, double* __restrict__ G, int n)      \
+    {                                                                                               \
+        const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;                      \
+        if (q >= b.total) return;                                                                   \
+        const int i = find_bra(b.offs, b.nbra, q);                                                  \
+        const int j = b.kbeg[i] + (int)(q - b.offs[i]);                                             \
+        const int bp = b.bra[i], kp = b.ket[j];                                                     \
+        double I[(NA) * (NB) * (NC) * (ND)];                                                        \
+        eri_##TAG<double, 0>(P, bp, kp, I);                                                         \
+        const int fa = P.fa[bp], fb = P.fb[bp], fc = P.fa[kp], fd = P.fb[kp];                       \
+        const size_t nn = (size_t)n;                                                                \
+        for (int ia = 0; ia < (NA); ++ia)                                                           \
+            for (int ib = 0; ib < (NB); ++ib)                                                       \
+                for (int ic = 0; ic < (NC); ++ic)                                                   \
+                    for (int id = 0; id < (ND); ++id) {                                             \
+                        const double v = I[((ia * (NB) + ib) * (NC) + ic) * (ND) + id];             \
+                        const size_t a = fa + ia, bb = fb + ib, c = fc + ic, d = fd + id;           \
+                        G[((a * nn + bb) * nn + c) * nn + d] = v;                                   \
+                        G[((bb * nn + a) * nn + c) * nn + d] = v;                                   \
+                        G[((a * nn + bb) * nn + d) * nn + c] = v;                                   \
+                        G[((bb * nn + a) * nn + d) * nn + c] = v;                                   \
+                        G[((c * nn + d) * nn + a) * nn + bb] = v;                                   \
+                        G[((d * nn + c) * nn + a) * nn + bb] = v;                                   \
+                        G[((c * nn + d) * nn + bb) * nn + a] = v;                                   \
+                        G[((d * nn + c) * nn + bb) * nn + a] = v;                                   \
+                    }                                                                               \
+    }
+
+// Schwarz factors Q_ab = sqrt(max_{m in a, n in b} |(mn|mn)|) for a list of pairs of one class.
+#define MESS_DEFINE_SCHWARZ_KERNEL(TAG, NA, NB)                                                    \
+    __global__ void __launch_bounds__(MESS_THREADS)                                                 \
+    k_schwarz_##TAG(const int* __restrict__ pairs, int npairs, const PairTable<double> P,           \
+                    double* __restrict__ Q)                                                         \
+    {                                                                                               \
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;                                        \
+        if (t >= npairs) return;                                                                    \
+        const int p = pairs[t];                                                                     \
+        double I[(NA) * (NB) * (NA) * (NB)];                                                        \
+        eri_##TAG<double, 0>(P, p, p, I);                                                           \
+        double m = 0.0;                                                                             \
+        for (int ia = 0; ia < (NA); ++ia)                                                           \
+            for (int ib = 0; ib < (NB); ++ib)                                                       \
+                m = fmax(m, fabs(I[((ia * (NB) + ib) * (NA) + ia) * (NB) + ib]));                   \
+        Q[p] = sqrt(m);                                                                             \
+    }
+
+// ------------------------------------------------------------------------------------------
+// Op-program evaluation of one shell quartet (large angular classes).  The program is the same
+// VRR / HRR sequence as the straight-line code, with values packed into NV / NH slots:
+//   VRR op (uint4): x = kind | dir<<2 | m1<<4 | m2<<8 | target<<16, y = s1 | s2<<16,
+//                   z = s3 | s4<<16, w = s5
+//     kind 0: V[t] = F[s1] (base [00|00]^(m), prefactor included)
+//     kind 1: V[t] = PA_d V[s1] + WP_d V[s2] + m1/(2 zeta) (V[s3] - rho/zeta V[s4])
+//     kind 2: V[t] = QC_d V[s1] + WQ_d V[s2] + m1/(2 eta) (V[s3] - rho/eta V[s4])
+//                    + m2/(2(zeta+eta)) V[s5]
+//     kind 3: H[s1] += V[t]  (contraction into [e0|f0])
+//   HRR op (uint2): x = target | dir<<16 | side<<18, y = s1 | s2<<16:
+//     H[t] = H[s1] + X_d H[s2],  X = A - B (side 0) or C - D (side 1)
+//   I[k] = fscale[k] * H[fslot[k]]  (per-component normalisation)
+// Every thread runs the same op sequence, so the kind / direction branches are warp-uniform.
+// ------------------------------------------------------------------------------------------
+template <typename R> __device__ __forceinline__ R pick3(int d, R x, R y, R z)
+{
+    return d == 0 ? x : (d == 1 ? y : z);
+}
+
+template <typename R, int BMODE, int L, int NV, int NH, int NACC, int NVOPS, int NHOPS, int NINT>
+__device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int kp,
+                                            const uint4* __restrict__ vprog, const uint2* __restrict__ hprog,
+                                            const int* __restrict__ fslot, const double* __restrict__ fscale,
+                                            R* I)
+{
+    R V[NV];
+    R H[NH];
+#pragma unroll 1
+    for (int k = 0; k < NACC; ++k) H[k] = R(0);
+    const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];
+    const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
+    const R ACx = R(P.C[3 * bp] - P.C[3 * kp]), ACy = R(P.C[3 * bp + 1] - P.C[3 * kp + 1]);
+    const R ACz = R(P.C[3 * bp + 2] - P.C[3 * kp + 2]);
+#pragma unroll 1
+    for (int ib = b0; ib < b1; ++ib) {
+        const PrimPair<R> pb = P.load(ib);
+#pragma unroll 1
+        for (int ik = k0; ik < k1; ++ik) {
+            const PrimPair<R> pk = P.load(ik);
+            const R rz = R(1) / (pb.zeta + pk.zeta);
+            const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;
+            const R PQx = pb.PAx - pk.PAx + ACx, PQy = pb.PAy - pk.PAy + ACy, PQz = pb.PAz - pk.PAz + ACz;
+            const R WPx = -roz * PQx, WPy = -roz * PQy, WPz = -roz * PQz;
+            const R WQx = roe * PQx, WQy = roe * PQy, WQz = roe * PQz;
+            const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);
+            const R pref = pb.K * pk.K * prefactor_sqrt(rz);
+            R F[L + 1];
+            boys_eval<R, L, BMODE>(T, F, P.boys64, P.boys32);
+#pragma unroll
+            for (int m = 0; m <= L; ++m) F[m] *= pref;
+#pragma unroll 1
+            for (int o = 0; o < NVOPS; ++o) {
+                const uint4 w = __ldg(vprog + o);
+                const int kind = w.x & 3, d = (w.x >> 2) & 3;
+                const int m1 = (w.x >> 4) & 15, m2 = (w.x >> 8) & 15, t = w.x >> 16;
+                const int s1 = w.y & 0xffff, s2 = w.y >> 16;
+                if (kind == 0) {
+                    R f = F[0];
+#pragma unroll
+                    for (int m = 1; m <= L; ++m) f = (s1 == m) ? F[m] : f;
+                    V[t] = f;
+                } else if (kind == 3) {
+                    H[s1] += V[t];
+                } else {
+                    R v;
+                    if (kind == 1) {
+                        v = pick3(d, pb.PAx, pb.PAy, pb.PAz) * V[s1] + pick3(d, WPx, WPy, WPz) * V[s2];
+                        if (m1) v += R(m1) * pb.oo2z * (V[w.z & 0xffff] - roz * V[w.z >> 16]);
+                    } else {
+                        v = pick3(d, pk.PAx, pk.PAy, pk.PAz) * V[s1] + pick3(d, WQx, WQy, WQz) * V[s2];
+                        if (m1) v += R(m1) * pk.oo2z * (V[w.z & 0xffff] - roe * V[w.z >> 16]);
+                        if (m2) v += R(m2) * oo2ze * V[w.w];
+                    }
+                    V[t] = v;
+                }
+            }
+        }
+    }
+    const R ABx = R(P.AB[3 * bp]), ABy = R(P.AB[3 * bp + 1]), ABz = R(P.AB[3 * bp + 2]);
+    const R CDx = R(P.AB[3 * kp]), CDy = R(P.AB[3 * kp + 1]), CDz = R(P.AB[3 * kp + 2]);
+#pragma unroll 1
+    for (int o = 0; o < NHOPS; ++o) {
+        const uint2 w = __ldg(hprog + o);
+        const int t = w.x & 0xffff, d = (w.x >> 16) & 3, side = (w.x >> 18) & 1;
+        const R X = side ? pick3(d, CDx, CDy, CDz) : pick3(d, ABx, ABy, ABz);
+        H[t] = H[w.y & 0xffff] + X * H[w.y >> 16];
+    }
+#pragma unroll 1
+    for (int k = 0; k < NINT; ++k) I[k] = R(__ldg(fscale + k)) * H[__ldg(fslot + k)];
+}

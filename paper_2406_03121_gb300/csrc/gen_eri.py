@@ -1,0 +1,642 @@
+#!/usr/bin/env python3
+"""Generates the per-angular-class ERI device code (Obara-Saika VRR + Head-Gordon-Pople HRR).
+
+For every shell-quartet class (la lb | lc ld) with la >= lb, lc >= ld and the higher pair class on
+the bra side, emit straight-line CUDA that, for one shell quartet,
+  1. loops over primitive quartets: Boys F_m(T), m = 0..L, then the VRR
+        [e+1_i,0|00]^(m) = PA_i [e0|00]^(m) + WP_i [e0|00]^(m+1)
+                           + e_i/(2 zeta) ([e-1_i,0|00]^(m) - rho/zeta [e-1_i,0|00]^(m+1))
+        [e0|f+1_i,0]^(m) = QC_i [e0|f0]^(m) + WQ_i [e0|f0]^(m+1)
+                           + f_i/(2 eta) ([e0|f-1_i,0]^(m) - rho/eta [e0|f-1_i,0]^(m+1))
+                           + e_i/(2(zeta+eta)) [e-1_i,0|f0]^(m+1)
+     accumulating the contracted [e0|f0] for la <= |e| <= la+lb, lc <= |f| <= lc+ld;
+  2. applies the HRR on the contracted sums,
+        (a, b+1_i| = (a+1_i, b| + AB_i (a, b|,      |c, d+1_i) = |c+1_i, d) + CD_i |c, d);
+  3. scales each Cartesian component by sqrt((2L-1)!! / ((2l-1)!!(2m-1)!!(2n-1)!!)), which turns
+     the x^L-normalised contraction into per-component unit-norm functions.
+Writes ``eri_class_<la><lb><lc><ld>.cuh`` files plus ``eri_classes.h`` (the class table) into the
+output directory.  Run: ``gen_eri.py <outdir>``.
+"""
+from __future__ import annotations
+
+import math
+import os
+import sys
+
+PAIR_CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+QUARTET_CLASSES = [(PAIR_CLASSES[i], PAIR_CLASSES[j])
+                   for i in range(len(PAIR_CLASSES)) for j in range(i + 1)]
+
+
+def cart(l):
+    return [(lx, ly, l - lx - ly) for lx in range(l, -1, -1) for ly in range(l - lx, -1, -1)]
+
+
+def ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def cidx(t):
+    """index of Cartesian triple t within cart(sum(t))"""
+    return cart(sum(t)).index(tuple(t))
+
+
+def sub(v, i, k=1):
+    w = list(v)
+    w[i] -= k
+    return tuple(w)
+
+
+def add(v, i, k=1):
+    w = list(v)
+    w[i] += k
+    return tuple(w)
+
+
+def dfact(k):
+    r = 1
+    while k > 1:
+        r *= k
+        k -= 2
+    return r
+
+
+def comp_scale(t):
+    L = sum(t)
+    return math.sqrt(dfact(2 * L - 1) / (dfact(2 * t[0] - 1) * dfact(2 * t[1] - 1) * dfact(2 * t[2] - 1)))
+
+
+def pick_dir(v):
+    """direction used to lower a Cartesian triple: its largest component (ties: lowest axis)"""
+    best = 0
+    for i in range(3):
+        if v[i] > v[best]:
+            best = i
+    return best
+
+
+XYZ = "xyz"
+
+
+class VRR:
+    def __init__(self, la, lb, lc, ld):
+        self.la, self.lb, self.lc, self.ld = la, lb, lc, ld
+        self.L = la + lb + lc + ld
+        self.order = []
+        self.names = {}
+        self.es = [e for E in range(la, la + lb + 1) for e in cart(E)]
+        self.fs = [f for F in range(lc, lc + ld + 1) for f in cart(F)]
+        for e in self.es:
+            for f in self.fs:
+                self._need(e, f, 0)
+
+    def _need(self, e, f, m):
+        key = (e, f, m)
+        if key in self.names:
+            return
+        deps = []
+        if sum(f) > 0:
+            i = pick_dir(f)
+            f1 = sub(f, i)
+            deps = [(e, f1, m), (e, f1, m + 1)]
+            if f1[i] >= 1:
+                deps += [(e, sub(f1, i), m), (e, sub(f1, i), m + 1)]
+            if e[i] >= 1:
+                deps += [(sub(e, i), f1, m + 1)]
+        elif sum(e) > 0:
+            i = pick_dir(e)
+            e1 = sub(e, i)
+            deps = [(e1, f, m), (e1, f, m + 1)]
+            if e1[i] >= 1:
+                deps += [(sub(e1, i), f, m), (sub(e1, i), f, m + 1)]
+        for d in deps:
+            self._need(*d)
+        self.names[key] = f"v{len(self.order)}"
+        self.order.append(key)
+
+    def emit(self, out, indent):
+        flops = 0
+        for (e, f, m) in self.order:
+            nm = self.names[(e, f, m)]
+            if sum(e) == 0 and sum(f) == 0:
+                out.append(f"{indent}const R {nm} = F[{m}];")
+                continue
+            if sum(f) > 0:
+                i = pick_dir(f)
+                f1 = sub(f, i)
+                x = XYZ[i]
+                terms = f"QC{x} * {self.names[(e, f1, m)]} + WQ{x} * {self.names[(e, f1, m + 1)]}"
+                flops += 3
+                if f1[i] >= 1:
+                    f2 = sub(f1, i)
+                    terms += (f" + R({f1[i]}) * oo2e * ({self.names[(e, f2, m)]}"
+                              f" - roe * {self.names[(e, f2, m + 1)]})")
+                    flops += 4
+                if e[i] >= 1:
+                    terms += f" + R({e[i]}) * oo2ze * {self.names[(sub(e, i), f1, m + 1)]}"
+                    flops += 3
+            else:
+                i = pick_dir(e)
+                e1 = sub(e, i)
+                x = XYZ[i]
+                terms = f"PA{x} * {self.names[(e1, f, m)]} + WP{x} * {self.names[(e1, f, m + 1)]}"
+                flops += 3
+                if e1[i] >= 1:
+                    e2 = sub(e1, i)
+                    terms += (f" + R({e1[i]}) * oo2z * ({self.names[(e2, f, m)]}"
+                              f" - roz * {self.names[(e2, f, m + 1)]})")
+                    flops += 4
+            out.append(f"{indent}const R {nm} = {terms};")
+        return flops
+
+
+def hrr_bra(la, lb, fs, es, out, indent, accname):
+    """(a b| f] for a in cart(la), b in cart(lb), every f: from acc[e][f]. Returns (names, flops)."""
+    nf = len(fs)
+    eidx = {e: k for k, e in enumerate(es)}
+    memo = {}
+    counter = [0]
+    flops = [0]
+
+    def get(a, b, fi):
+        key = (a, b, fi)
+        if key in memo:
+            return memo[key]
+        if sum(b) == 0:
+            nm = f"{accname}[{eidx[a] * nf + fi}]"
+            memo[key] = nm
+            return nm
+        i = pick_dir(b)
+        b1 = sub(b, i)
+        t1 = get(add(a, i), b1, fi)
+        t2 = get(a, b1, fi)
+        nm = f"hb{counter[0]}"
+        counter[0] += 1
+        out.append(f"{indent}const R {nm} = {t1} + AB{XYZ[i]} * {t2};")
+        flops[0] += 2
+        memo[key] = nm
+        return nm
+
+    res = {}
+    for fi in range(nf):
+        for a in cart(la):
+            for b in cart(lb):
+                res[(a, b, fi)] = get(a, b, fi)
+    return res, flops[0]
+
+
+def hrr_ket(lc, ld, fs, brares, la, lb, out, indent):
+    """(ab|cd) from (ab|f]."""
+    fidx = {f: k for k, f in enumerate(fs)}
+    memo = {}
+    counter = [0]
+    flops = [0]
+
+    def get(ab, c, d):
+        key = (ab, c, d)
+        if key in memo:
+            return memo[key]
+        if sum(d) == 0:
+            nm = brares[(ab[0], ab[1], fidx[c])]
+            memo[key] = nm
+            return nm
+        i = pick_dir(d)
+        d1 = sub(d, i)
+        t1 = get(ab, add(c, i), d1)
+        t2 = get(ab, c, d1)
+        nm = f"hk{counter[0]}"
+        counter[0] += 1
+        out.append(f"{indent}const R {nm} = {t1} + CD{XYZ[i]} * {t2};")
+        flops[0] += 2
+        memo[key] = nm
+        return nm
+
+    res = {}
+    for a in cart(la):
+        for b in cart(lb):
+            for c in cart(lc):
+                for d in cart(ld):
+                    res[(a, b, c, d)] = get((a, b), c, d)
+    return res, flops[0]
+
+
+# ------------------------------------------------------------------------------------------------
+# Op programs for the generic (interpreted) kernel.  The VRR / HRR sequences are the same as in the
+# straight-line code; slots are assigned by a linear scan over live intervals so that the per-thread
+# working arrays only hold the values that are live at the same time.
+# ------------------------------------------------------------------------------------------------
+def _linear_scan(n_values, defs_uses, pinned=()):
+    """defs_uses: list over op positions of (defined_value or None, [used values]).
+    Returns slot per value and the number of slots."""
+    last = {}
+    for pos, (d, uses) in enumerate(defs_uses):
+        for u in uses:
+            last[u] = pos
+    for v in pinned:
+        last[v] = len(defs_uses)
+    free = []
+    nslots = 0
+    slot = {}
+    for pos, (d, uses) in enumerate(defs_uses):
+        # release values whose last use is this op (after reading them)
+        if d is not None:
+            # allocate before releasing so the target never aliases a source of the same op
+            if free:
+                slot[d] = free.pop()
+            else:
+                slot[d] = nslots
+                nslots += 1
+            if d not in last:
+                last[d] = pos
+        for u in set(uses):
+            if last.get(u) == pos:
+                free.append(slot[u])
+        if d is not None and last[d] == pos and d not in pinned:
+            free.append(slot[d])
+    return slot, nslots
+
+
+def build_program(cls):
+    (la, lb), (lc, ld) = cls
+    v = VRR(la, lb, lc, ld)
+    nf = len(v.fs)
+    accidx = {}
+    for ei, e in enumerate(v.es):
+        for fi, f in enumerate(v.fs):
+            accidx[(e, f, 0)] = ei * nf + fi
+    # VRR ops: (kind, target, s1, s2, s3, s4, s5, dir, m1, m2); kind 0 base, 1 bra, 2 ket, 3 acc
+    raw = []
+    for key in v.order:
+        e, f, m = key
+        if sum(e) == 0 and sum(f) == 0:
+            raw.append((0, key, [], m, 0, 0, 0))
+        elif sum(f) > 0:
+            i = pick_dir(f)
+            f1 = sub(f, i)
+            srcs = [(e, f1, m), (e, f1, m + 1)]
+            m1 = f1[i]
+            srcs += [(e, sub(f1, i), m), (e, sub(f1, i), m + 1)] if m1 >= 1 else [None, None]
+            m2 = e[i]
+            srcs += [(sub(e, i), f1, m + 1)] if m2 >= 1 else [None]
+            raw.append((2, key, srcs, None, i, m1, m2))
+        else:
+            i = pick_dir(e)
+            e1 = sub(e, i)
+            srcs = [(e1, f, m), (e1, f, m + 1)]
+            m1 = e1[i]
+            srcs += [(sub(e1, i), f, m), (sub(e1, i), f, m + 1)] if m1 >= 1 else [None, None]
+            srcs += [None]
+            raw.append((1, key, srcs, None, i, m1, 0))
+        if key in accidx:
+            raw.append((3, key, [key], accidx[key], 0, 0, 0))
+    du = []
+    for (kind, key, srcs, extra, d, m1, m2) in raw:
+        uses = [x for x in srcs if x is not None]
+        du.append((key if kind != 3 else None, uses))
+    slot, nv = _linear_scan(len(v.order), du)
+    vrr_ops = []
+    for (kind, key, srcs, extra, d, m1, m2) in raw:
+        if kind == 0:
+            vrr_ops.append((0, slot[key], extra, 0, 0, 0, 0, 0, 0, 0))
+        elif kind == 3:
+            vrr_ops.append((3, slot[key], extra, 0, 0, 0, 0, 0, 0, 0))
+        else:
+            ss = [slot[x] if x is not None else 0 for x in srcs]
+            vrr_ops.append((kind, slot[key], ss[0], ss[1], ss[2], ss[3], ss[4], d, m1, m2))
+    # HRR ops on H: values 'acc k' first (pinned into slots 0..nacc-1), then bra/ket intermediates
+    nacc = len(v.es) * nf
+    eidx = {e: k for k, e in enumerate(v.es)}
+    fidx = {f: k for k, f in enumerate(v.fs)}
+    hops = []          # (target value, src1 value, src2 value, dir, side)
+    memo_b = {}
+
+    def gb(a, b, fi):
+        key = ("b", a, b, fi)
+        if key in memo_b:
+            return memo_b[key]
+        if sum(b) == 0:
+            val = ("acc", eidx[a] * nf + fi)
+        else:
+            i = pick_dir(b)
+            b1 = sub(b, i)
+            t1 = gb(add(a, i), b1, fi)
+            t2 = gb(a, b1, fi)
+            val = key
+            hops.append((val, t1, t2, i, 0))
+        memo_b[key] = val
+        return val
+    memo_k = {}
+
+    def gk(a, b, c, d):
+        key = ("k", a, b, c, d)
+        if key in memo_k:
+            return memo_k[key]
+        if sum(d) == 0:
+            val = gb(a, b, fidx[c])
+        else:
+            i = pick_dir(d)
+            d1 = sub(d, i)
+            t1 = gk(a, b, add(c, i), d1)
+            t2 = gk(a, b, c, d1)
+            val = key
+            hops.append((val, t1, t2, i, 1))
+        memo_k[key] = val
+        return val
+    finals = []
+    for a in cart(la):
+        for b in cart(lb):
+            for c in cart(lc):
+                for d in cart(ld):
+                    finals.append((gk(a, b, c, d), comp_scale(a) * comp_scale(b) * comp_scale(c) * comp_scale(d)))
+    # slot allocation for H: acc values pinned at 0..nacc-1 until their last use, finals pinned to the end
+    du = [(None, [])]  # position 0: all acc values defined (pre-existing)
+    for (t, s1, s2, d, side) in hops:
+        du.append((t, [s1, s2]))
+    final_vals = [f for f, _ in finals]
+    # custom scan: acc values occupy fixed slots; other values get slots >= nacc
+    last = {}
+    for pos, (d, uses) in enumerate(du):
+        for u in uses:
+            last[u] = pos
+    for fv in final_vals:
+        last[fv] = len(du)
+    hslot = {("acc", k): k for k in range(nacc)}
+    free = []
+    nh = nacc
+    for pos, (d, uses) in enumerate(du):
+        if d is not None:
+            if free:
+                hslot[d] = free.pop()
+            else:
+                hslot[d] = nh
+                nh += 1
+        for u in set(uses):
+            if last.get(u) == pos:
+                free.append(hslot[u])
+    hrr_ops = [(hslot[t], hslot[s1], hslot[s2], d, side) for (t, s1, s2, d, side) in hops]
+    fin = [(hslot[fv], sc) for fv, sc in finals]
+    return dict(vrr=vrr_ops, nv=nv, hrr=hrr_ops, nh=nh, fin=fin, nacc=nacc, L=la + lb + lc + ld,
+                na=ncart(la), nb=ncart(lb), nc=ncart(lc), nd=ncart(ld))
+
+
+def straight_line(info):
+    """classes emitted as straight-line register code (the rest run the op-program kernel)"""
+    return info["nacc"] <= 96 and info["nvrr"] <= 280
+
+
+def tag(cls):
+    (la, lb), (lc, ld) = cls
+    return f"{la}{lb}{lc}{ld}"
+
+
+def emit_class_straight(cls):
+    (la, lb), (lc, ld) = cls
+    t = tag(cls)
+    L = la + lb + lc + ld
+    v = VRR(la, lb, lc, ld)
+    na, nb, nc, nd = ncart(la), ncart(lb), ncart(lc), ncart(ld)
+    nint = na * nb * nc * nd
+    nacc = len(v.es) * len(v.fs)
+    lines = []
+    lines.append(f"// ---- class ({la}{lb}|{lc}{ld}): {len(v.order)} VRR entries, {nacc} contracted, {nint} integrals")
+    lines.append(f"template <typename R, int BMODE>")
+    lines.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, R* I)")
+    lines.append("{")
+    lines.append(f"    R acc[{nacc}];")
+    lines.append(f"#pragma unroll")
+    lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = R(0);")
+    lines.append("    const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];")
+    lines.append("    const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];")
+    lines.append("    // A - C in FP64, then P - Q = (P - A) - (Q - C) + (A - C): no absolute coordinates in R")
+    lines.append("    const R ACx = R(P.C[3 * bp] - P.C[3 * kp]), ACy = R(P.C[3 * bp + 1] - P.C[3 * kp + 1]);")
+    lines.append("    const R ACz = R(P.C[3 * bp + 2] - P.C[3 * kp + 2]);")
+    lines.append("#pragma unroll 1")
+    lines.append("    for (int ib = b0; ib < b1; ++ib) {")
+    lines.append("        const PrimPair<R> pb = P.load(ib);")
+    lines.append("#pragma unroll 1")
+    lines.append("        for (int ik = k0; ik < k1; ++ik) {")
+    lines.append("            const PrimPair<R> pk = P.load(ik);")
+    lines.append("            const R rz = R(1) / (pb.zeta + pk.zeta);")
+    lines.append("            const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;")
+    lines.append("            const R oo2z = pb.oo2z, oo2e = pk.oo2z;")
+    lines.append("            (void)roe; (void)roz; (void)oo2ze; (void)oo2z; (void)oo2e;")
+    lines.append("            const R PQx = pb.PAx - pk.PAx + ACx, PQy = pb.PAy - pk.PAy + ACy, PQz = pb.PAz - pk.PAz + ACz;")
+    lines.append("            const R PAx = pb.PAx, PAy = pb.PAy, PAz = pb.PAz;")
+    lines.append("            const R QCx = pk.PAx, QCy = pk.PAy, QCz = pk.PAz;")
+    lines.append("            const R WPx = -roz * PQx, WPy = -roz * PQy, WPz = -roz * PQz;")
+    lines.append("            const R WQx = roe * PQx, WQy = roe * PQy, WQz = roe * PQz;")
+    lines.append("            (void)PAx; (void)PAy; (void)PAz; (void)QCx; (void)QCy; (void)QCz;")
+    lines.append("            (void)WPx; (void)WPy; (void)WPz; (void)WQx; (void)WQy; (void)WQz;")
+    lines.append("            const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);")
+    lines.append("            const R pref = pb.K * pk.K * prefactor_sqrt(rz);")
+    lines.append(f"            R F[{L + 1}];")
+    lines.append(f"            boys_eval<R, {L}, BMODE>(T, F, P.boys64, P.boys32);")
+    lines.append("#pragma unroll")
+    lines.append(f"            for (int m = 0; m <= {L}; ++m) F[m] *= pref;")
+    body = []
+    vflops = v.emit(body, "            ")
+    lines += body
+    for ei, e in enumerate(v.es):
+        for fi, f in enumerate(v.fs):
+            lines.append(f"            acc[{ei * len(v.fs) + fi}] += {v.names[(e, f, 0)]};")
+    lines.append("        }")
+    lines.append("    }")
+    lines.append("    const R ABx = R(P.AB[3 * bp]), ABy = R(P.AB[3 * bp + 1]), ABz = R(P.AB[3 * bp + 2]);")
+    lines.append("    const R CDx = R(P.AB[3 * kp]), CDy = R(P.AB[3 * kp + 1]), CDz = R(P.AB[3 * kp + 2]);")
+    lines.append("    (void)ABx; (void)ABy; (void)ABz; (void)CDx; (void)CDy; (void)CDz;")
+    hb, hbf = hrr_bra(la, lb, v.fs, v.es, lines, "    ", "acc")
+    hk, hkf = hrr_ket(lc, ld, v.fs, hb, la, lb, lines, "    ")
+    k = 0
+    for a in cart(la):
+        for b in cart(lb):
+            for c in cart(lc):
+                for d in cart(ld):
+                    s = comp_scale(a) * comp_scale(b) * comp_scale(c) * comp_scale(d)
+                    if abs(s - 1.0) < 1e-15:
+                        lines.append(f"    I[{k}] = {hk[(a, b, c, d)]};")
+                    else:
+                        lines.append(f"    I[{k}] = R({s!r}) * {hk[(a, b, c, d)]};")
+                    k += 1
+    lines.append("}")
+    info = dict(tag=t, la=la, lb=lb, lc=lc, ld=ld, L=L, nvrr=len(v.order), vrr_flops=vflops,
+                hrr_flops=hbf + hkf, nacc=nacc, nint=nint)
+    return "\n".join(lines) + "\n", info
+
+
+def emit_class(cls):
+    body, info = emit_class_straight(cls)
+    if straight_line(info):
+        info["mode"] = "straight"
+        return body, info
+    (la, lb), (lc, ld) = cls
+    t = tag(cls)
+    pr = build_program(cls)
+    info["mode"] = "program"
+    info["nv_slots"], info["nh_slots"] = pr["nv"], pr["nh"]
+    L = []
+    L.append(f"// ---- class ({la}{lb}|{lc}{ld}): op program, {len(pr['vrr'])} VRR ops on {pr['nv']} slots, "
+             f"{len(pr['hrr'])} HRR ops on {pr['nh']} slots")
+    L.append(f"__device__ const uint4 vprog_{t}[{len(pr['vrr'])}] = {{")
+    for (kind, tg, s1, s2, s3, s4, s5, d, m1, m2) in pr["vrr"]:
+        w0 = kind | (d << 2) | (m1 << 4) | (m2 << 8) | (tg << 16)
+        L.append(f"    {{{w0}u, {s1 | (s2 << 16)}u, {s3 | (s4 << 16)}u, {s5}u}},")
+    L.append("};")
+    L.append(f"__device__ const uint2 hprog_{t}[{max(1, len(pr['hrr']))}] = {{")
+    for (tg, s1, s2, d, side) in pr["hrr"]:
+        L.append(f"    {{{tg | (d << 16) | (side << 18)}u, {s1 | (s2 << 16)}u}},")
+    if not pr["hrr"]:
+        L.append("    {0u, 0u},")
+    L.append("};")
+    L.append(f"__device__ const int fslot_{t}[{len(pr['fin'])}] = {{" + ", ".join(str(a) for a, _ in pr["fin"]) + "};")
+    L.append(f"__device__ const double fscale_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(b) for _, b in pr["fin"]) + "};")
+    L.append("template <typename R, int BMODE>")
+    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, R* I)")
+    L.append("{")
+    L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
+             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kp, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, I);")
+    L.append("}")
+    return "\n".join(L) + "\n", info
+
+
+def emit_digest(cls, unroll=True):
+    """J/K digestion of one shell quartet (see the kernel file for the accumulation convention).
+    unroll=True: density blocks staged in registers, loops fully unrolled (small classes);
+    unroll=False: compact loops reading the density through the read-only cache (large classes)."""
+    (la, lb), (lc, ld) = cls
+    t = tag(cls)
+    na, nb, nc, nd = ncart(la), ncart(lb), ncart(lc), ncart(ld)
+    PR = "#pragma unroll" if unroll else "#pragma unroll 1"
+    L = []
+    L.append(f"template <typename R>")
+    L.append(f"__device__ __forceinline__ void digest_{t}(const R* I, const DigestCtx& c, R s)")
+    L.append("{")
+    blocks = (("Dab", ("c.fa", na), ("c.fb", nb)), ("Dcd", ("c.fc", nc), ("c.fd", nd)),
+              ("Dac", ("c.fa", na), ("c.fc", nc)), ("Dad", ("c.fa", na), ("c.fd", nd)),
+              ("Dbc", ("c.fb", nb), ("c.fc", nc)), ("Dbd", ("c.fb", nb), ("c.fd", nd)))
+    dref = {}
+    for nm, (r0, nr), (c0, ncol) in blocks:
+        if unroll:
+            L.append(f"    R {nm}[{nr * ncol}];")
+            L.append(PR)
+            L.append(f"    for (int i = 0; i < {nr}; ++i)")
+            L.append(PR)
+            L.append(f"        for (int j = 0; j < {ncol}; ++j) {nm}[i * {ncol} + j] = R(c.D[(size_t)({r0} + i) * c.n + {c0} + j]);")
+            dref[nm] = lambda a, b, nm=nm, ncol=ncol: f"{nm}[{a} * {ncol} + {b}]"
+        else:
+            dref[nm] = lambda a, b, r0=r0, c0=c0: f"R(__ldg(c.D + (size_t)({r0} + {a}) * c.n + {c0} + {b}))"
+    I = f"I[((i * {nb} + j) * {nc} + k) * {nd} + l]"
+    # J_ab
+    L += [PR, f"    for (int i = 0; i < {na}; ++i)", PR, f"        for (int j = 0; j < {nb}; ++j) {{",
+          "            R t = R(0);", PR, f"            for (int k = 0; k < {nc}; ++k)", PR,
+          f"                for (int l = 0; l < {nd}; ++l) t += {I} * {dref['Dcd']('k', 'l')};",
+          "            jk_add(c.J, (size_t)(c.fa + i) * c.n + c.fb + j, s * t, c.warp_reduce_ab);", "        }"]
+    # J_cd
+    L += [PR, f"    for (int k = 0; k < {nc}; ++k)", PR, f"        for (int l = 0; l < {nd}; ++l) {{",
+          "            R t = R(0);", PR, f"            for (int i = 0; i < {na}; ++i)", PR,
+          f"                for (int j = 0; j < {nb}; ++j) t += {I} * {dref['Dab']('i', 'j')};",
+          "            jk_add(c.J, (size_t)(c.fc + k) * c.n + c.fd + l, s * t, false);", "        }"]
+    # K blocks: K_ac (sum b,d D_bd), K_ad (sum b,c D_bc), K_bc (sum a,d D_ad), K_bd (sum a,c D_ac)
+    for (o1, n1, f1), (o2, n2, f2), (s1, m1), (s2, m2), Dn in (
+            (("i", na, "c.fa"), ("k", nc, "c.fc"), ("j", nb), ("l", nd), "Dbd"),
+            (("i", na, "c.fa"), ("l", nd, "c.fd"), ("j", nb), ("k", nc), "Dbc"),
+            (("j", nb, "c.fb"), ("k", nc, "c.fc"), ("i", na), ("l", nd), "Dad"),
+            (("j", nb, "c.fb"), ("l", nd, "c.fd"), ("i", na), ("k", nc), "Dac")):
+        L += [PR, f"    for (int {o1} = 0; {o1} < {n1}; ++{o1})", PR,
+              f"        for (int {o2} = 0; {o2} < {n2}; ++{o2}) {{", "            R t = R(0);", PR,
+              f"            for (int {s1} = 0; {s1} < {m1}; ++{s1})", PR,
+              f"                for (int {s2} = 0; {s2} < {m2}; ++{s2}) t += {I} * {dref[Dn](s1, s2)};",
+              f"            jk_add(c.K, (size_t)({f1} + {o1}) * c.n + {f2} + {o2}, s * t, false);", "        }"]
+    L.append("}")
+    return "\n".join(L) + "\n"
+
+
+def main(outdir):
+    os.makedirs(outdir, exist_ok=True)
+    infos = []
+    for cls in QUARTET_CLASSES:
+        body, info = emit_class(cls)
+        dig = emit_digest(cls, unroll=(info['mode'] == 'straight'))
+        path = os.path.join(outdir, f"eri_class_{info['tag']}.cuh")
+        text = ("// Generated by gen_eri.py: do not edit.\n#pragma once\n#include \"eri_common.cuh\"\n\n"
+                + body + "\n" + dig)
+        old = open(path).read() if os.path.exists(path) else None
+        if old != text:
+            with open(path, "w") as fh:
+                fh.write(text)
+        infos.append(info)
+    # one translation unit per class: kernels + launcher
+    for cls, info in zip(QUARTET_CLASSES, infos):
+        (la, lb), (lc, ld) = cls
+        t = info["tag"]
+        na, nb, nc, nd = ncart(la), ncart(lb), ncart(lc), ncart(ld)
+        diag = (la, lb) == (lc, ld)
+        u = ["// Generated by gen_eri.py: do not edit.", f'#include "eri_class_{t}.cuh"', '#include "eri_launch.h"', "",
+             f"MESS_DEFINE_CLASS_KERNELS({t}, {na}, {nb}, {nc}, {nd})"]
+        if diag:
+            u.append(f"MESS_DEFINE_SCHWARZ_KERNEL({t}, {na}, {nb})")
+        u += ["", f"cudaError_t mess_launch_{t}(const ClassLaunchArgs& a)", "{",
+              "    const int T = MESS_THREADS;",
+              "    if (a.kind == MESS_KIND_SCHWARZ) {",
+              ]
+        if diag:
+            u += ["        if (a.npairs <= 0) return cudaSuccess;",
+                  f"        k_schwarz_{t}<<<(a.npairs + T - 1) / T, T, 0, a.stream>>>(a.pairs, a.npairs, *a.P64_ptr, a.out);",
+                  "        return cudaGetLastError();"]
+        else:
+            u += ["        return cudaErrorInvalidValue;"]
+        u += ["    }",
+              "    if (a.bin.total <= 0) return cudaSuccess;",
+              "    const long long nblk = (a.bin.total + T - 1) / T;",
+              "    if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
+              "    const dim3 g((unsigned)nblk);",
+              "    if (a.kind == MESS_KIND_STORE) {",
+              f"        k_store_{t}<<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.out, a.n);",
+              "    } else if (a.mode == MESS_MODE_FP64) {",
+              f"        k_jk_{t}<double, 0><<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
+              "    } else if (a.mode == MESS_MODE_MIXED) {",
+              f"        k_jk_{t}<float, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              "    } else {",
+              f"        k_jk_{t}<float, 2><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              "    }",
+              "    return cudaGetLastError();",
+              "}"]
+        text = "\n".join(u) + "\n"
+        path = os.path.join(outdir, f"eri_class_{t}.cu")
+        old = open(path).read() if os.path.exists(path) else None
+        if old != text:
+            with open(path, "w") as fh:
+                fh.write(text)
+    # dispatch table
+    d = ["// Generated by gen_eri.py: do not edit.", '#include "eri_launch.h"', ""]
+    for info in infos:
+        d.append(f"cudaError_t mess_launch_{info['tag']}(const ClassLaunchArgs& a);")
+    d += ["", "const mess_class_launcher MESS_CLASS_LAUNCHERS[MESS_NUM_QCLASS] = {"]
+    for info in infos:
+        d.append(f"    mess_launch_{info['tag']},")
+    d.append("};")
+    text = "\n".join(d) + "\n"
+    path = os.path.join(outdir, "eri_dispatch.cu")
+    old = open(path).read() if os.path.exists(path) else None
+    if old != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+    # class table (host + device readable)
+    tab = ["// Generated by gen_eri.py: do not edit.", "#pragma once", "",
+           f"#define MESS_NUM_QCLASS {len(QUARTET_CLASSES)}", "",
+           "typedef struct { int la, lb, lc, ld, L, nint, nacc, nvrr; long vrr_flops, hrr_flops; } mess_qclass_info;",
+           "static const mess_qclass_info MESS_QCLASS[MESS_NUM_QCLASS] = {"]
+    for f in infos:
+        tab.append(f"    {{{f['la']}, {f['lb']}, {f['lc']}, {f['ld']}, {f['L']}, {f['nint']}, {f['nacc']}, "
+                   f"{f['nvrr']}, {f['vrr_flops']}, {f['hrr_flops']}}},")
+    tab.append("};")
+    text = "\n".join(tab) + "\n"
+    path = os.path.join(outdir, "eri_classes.h")
+    old = open(path).read() if os.path.exists(path) else None
+    if old != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+    return infos
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "_gen")

@@ -1,0 +1,686 @@
+// Host runtime of the library: basis construction, primitive-pair tables, Schwarz factors,
+// quartet bins and the C ABI entry points of include/mess.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "mess_internal.h"
+
+// ------------------------------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+void mess_set_error(const char* fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+extern "C" const char* mess_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------------------------------ basis file
+namespace {
+
+const char* kSymbols[] = {"", "H", "He", "Li", "Be", "B", "C", "N", "O", "F", "Ne"};
+
+struct FileShell { int l; std::vector<double> a, d; };
+
+bool parse_basis_file(const char* path, std::map<std::string, std::vector<FileShell>>& out)
+{
+    std::ifstream in(path);
+    if (!in) { mess_set_error("cannot open basis file '%s'", path ? path : "(null)"); return false; }
+    std::string line;
+    std::vector<FileShell>* cur = nullptr;
+    int lineno = 0;
+    auto strip = [](std::string s) {
+        size_t h = s.find('#');
+        if (h != std::string::npos) s = s.substr(0, h);
+        return s;
+    };
+    while (std::getline(in, line)) {
+        ++lineno;
+        line = strip(line);
+        std::istringstream ss(line);
+        std::string tok;
+        if (!(ss >> tok)) continue;
+        if (tok == "element") {
+            std::string sym;
+            if (!(ss >> sym)) { mess_set_error("%s:%d: element without symbol", path, lineno); return false; }
+            cur = &out[sym];
+            continue;
+        }
+        if (!cur) { mess_set_error("%s:%d: shell before any element line", path, lineno); return false; }
+        int nprim = 0;
+        if (!(ss >> nprim) || nprim <= 0 || nprim > 64) {
+            mess_set_error("%s:%d: bad primitive count", path, lineno);
+            return false;
+        }
+        std::string kind = tok;
+        for (auto& c : kind) c = (char)toupper(c);
+        bool sp = kind == "SP";
+        int l = kind == "S" ? 0 : kind == "P" ? 1 : kind == "D" ? 2 : (sp ? 0 : -1);
+        if (l < 0) { mess_set_error("%s:%d: unsupported shell type '%s'", path, lineno, tok.c_str()); return false; }
+        FileShell s0{l, {}, {}}, s1{1, {}, {}};
+        for (int k = 0; k < nprim; ++k) {
+            std::string pl;
+            do {
+                if (!std::getline(in, pl)) { mess_set_error("%s: truncated shell", path); return false; }
+                ++lineno;
+                pl = strip(pl);
+            } while (pl.find_first_not_of(" \t\r") == std::string::npos);
+            std::istringstream ps(pl);
+            double a, c0, c1 = 0.0;
+            if (!(ps >> a >> c0) || (sp && !(ps >> c1)) || !(a > 0.0)) {
+                mess_set_error("%s:%d: bad primitive line", path, lineno);
+                return false;
+            }
+            s0.a.push_back(a); s0.d.push_back(c0);
+            if (sp) { s1.a.push_back(a); s1.d.push_back(c1); }
+        }
+        cur->push_back(s0);
+        if (sp) cur->push_back(s1);
+    }
+    return true;
+}
+
+double dfact(int k)
+{
+    double r = 1.0;
+    while (k > 1) { r *= k; k -= 2; }
+    return r;
+}
+
+int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+int pclass_of(int la, int lb)   // la >= lb
+{
+    static const int tab[3][3] = {{0, -1, -1}, {1, 2, -1}, {3, 4, 5}};
+    return tab[la][lb];
+}
+
+int qclass_of(int p1, int p2)   // p1 >= p2
+{
+    return p1 * (p1 + 1) / 2 + p2;
+}
+
+// Contraction coefficients of one shell: each primitive normalised for its x^l component and the
+// contraction renormalised so that the contracted x^l function has unit norm.
+void normalise_shell(HostShell& s, const std::vector<double>& d)
+{
+    const int l = s.l;
+    const double pi = M_PI;
+    std::vector<double> c(s.K);
+    for (int k = 0; k < s.K; ++k) {
+        const double a = s.alpha[k];
+        c[k] = d[k] * pow(2.0 * a / pi, 0.75) * pow(4.0 * a, 0.5 * l) / sqrt(dfact(2 * l - 1));
+    }
+    double S = 0.0;
+    for (int i = 0; i < s.K; ++i)
+        for (int j = 0; j < s.K; ++j) {
+            const double p = s.alpha[i] + s.alpha[j];
+            S += c[i] * c[j] * pow(pi / p, 1.5) * dfact(2 * l - 1) / pow(2.0 * p, l);
+        }
+    s.coef.resize(s.K);
+    for (int k = 0; k < s.K; ++k) s.coef[k] = c[k] / sqrt(S);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------ bins
+mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
+{
+    BinSet& B = b->bins;
+    if (B.tau == tau && B.tau64 == tau64 && B.split == split) return MESS_OK;
+    B.parts.clear();
+    std::vector<int> bra, kbeg;
+    std::vector<long long> offs;
+    for (int p1 = 0; p1 < MESS_NUM_PCLASS; ++p1) {
+        for (int p2 = 0; p2 <= p1; ++p2) {
+            const std::vector<int>& bl = b->class_list[p1];
+            const std::vector<int>& kl = b->class_list[p2];
+            if (bl.empty() || kl.empty()) continue;
+            const bool same = p1 == p2;
+            const int nk = (int)kl.size();
+            std::vector<double> qk(nk);
+            std::vector<long long> fpre(nk + 1, 0), ppre(nk + 1, 0);
+            for (int j = 0; j < nk; ++j) {
+                const int pk = kl[j];
+                qk[j] = b->Q[pk];
+                const int nc = ncart(b->shells[b->pair_a[pk]].l), nd = ncart(b->shells[b->pair_b[pk]].l);
+                const long long nfp = b->pair_a[pk] == b->pair_b[pk] ? (long long)nc * (nc + 1) / 2 : (long long)nc * nd;
+                fpre[j + 1] = fpre[j] + nfp;
+                ppre[j + 1] = ppre[j] + b->pp_n[pk];
+            }
+            // number of kets j (Q descending) with qi * qk[j] >= t
+            auto count_ge = [&](double qi, double t) -> int {
+                if (t <= 0.0) return nk;
+                int lo = 0, hi = nk;   // first j with qi*qk[j] < t
+                while (lo < hi) {
+                    int mid = (lo + hi) / 2;
+                    if (qi * qk[mid] >= t) lo = mid + 1; else hi = mid;
+                }
+                return lo;
+            };
+            const int nparts = split == 2 ? 2 : 1;
+            for (int part = 0; part < nparts; ++part) {
+                const int fp64 = split == 0 ? 1 : (split == 1 ? 0 : (part == 0 ? 1 : 0));
+                BinPart bp;
+                bp.qclass = qclass_of(p1, p2);
+                bp.fp64 = fp64;
+                bp.bra_off = (int)bra.size();
+                bp.ket_list = p2;
+                bp.offs_off = offs.size();
+                bp.total = 0;
+                bp.fn_quartets = 0;
+                bp.prim_quartets = 0;
+                for (int i = 0; i < (int)bl.size(); ++i) {
+                    const int pb = bl[i];
+                    const double qi = b->Q[pb];
+                    int cnt = count_ge(qi, tau);
+                    if (same) cnt = std::min(cnt, i + 1);
+                    int beg = 0, end = cnt;
+                    if (split == 2) {
+                        const int c64 = tau64 > 0.0 ? std::min(count_ge(qi, tau64), cnt) : 0;
+                        if (part == 0) end = c64; else beg = c64;
+                    }
+                    if (end <= beg) continue;
+                    bra.push_back(pb);
+                    kbeg.push_back(beg);
+                    offs.push_back(bp.total);
+                    bp.total += end - beg;
+                    const int na = ncart(b->shells[b->pair_a[pb]].l), nb = ncart(b->shells[b->pair_b[pb]].l);
+                    const long long nfb = b->pair_a[pb] == b->pair_b[pb] ? (long long)na * (na + 1) / 2 : (long long)na * nb;
+                    bp.fn_quartets += nfb * (fpre[end] - fpre[beg]);
+                    if (same && beg <= i && i < end) bp.fn_quartets += nfb * (nfb + 1) / 2 - nfb * nfb;
+                    bp.prim_quartets += (long long)b->pp_n[pb] * (ppre[end] - ppre[beg]);
+                }
+                bp.nbra = (int)bra.size() - bp.bra_off;
+                offs.push_back(bp.total);
+                if (bp.nbra > 0) B.parts.push_back(bp);
+                else offs.resize(bp.offs_off);
+            }
+        }
+    }
+    if (B.bra.upload(bra) != cudaSuccess || B.kbeg.upload(kbeg) != cudaSuccess || B.offs.upload(offs) != cudaSuccess) {
+        mess_set_error("uploading quartet bins failed");
+        B.tau = -1.0;
+        return MESS_ECUDA;
+    }
+    B.tau = tau;
+    B.tau64 = tau64;
+    B.split = split;
+    return MESS_OK;
+}
+
+static BinLaunch bin_launch(const mess_basis* b, const BinPart& p)
+{
+    BinLaunch L;
+    L.bra = b->bins.bra.p + p.bra_off;
+    L.kbeg = b->bins.kbeg.p + p.bra_off;
+    L.offs = b->bins.offs.p + p.offs_off;
+    L.ket = b->d_class_list[p.ket_list].p;
+    L.nbra = p.nbra;
+    L.total = p.total;
+    return L;
+}
+
+// ------------------------------------------------------------------------------------------ create
+static mess_status build_basis(mess_basis* b, const char* basis_file)
+{
+    std::map<std::string, std::vector<FileShell>> data;
+    if (!parse_basis_file(basis_file, data)) return MESS_EINVAL;
+    int f0 = 0;
+    for (int a = 0; a < b->natom; ++a) {
+        const int z = b->Z[a];
+        if (z <= 0 || z > 10) { mess_set_error("unsupported atomic number %d", z); return MESS_EINVAL; }
+        auto it = data.find(kSymbols[z]);
+        if (it == data.end()) { mess_set_error("element %s not in basis file %s", kSymbols[z], basis_file); return MESS_EINVAL; }
+        for (const FileShell& fs : it->second) {
+            if (fs.l > MESS_LMAX) { mess_set_error("angular momentum %d not supported", fs.l); return MESS_EINVAL; }
+            HostShell s;
+            s.l = fs.l;
+            s.K = (int)fs.a.size();
+            s.atom = a;
+            s.f0 = f0;
+            for (int x = 0; x < 3; ++x) s.R[x] = b->xyz[3 * a + x];
+            s.alpha = fs.a;
+            normalise_shell(s, fs.d);
+            f0 += ncart(s.l);
+            b->shells.push_back(s);
+        }
+        b->nelec += z;
+    }
+    b->nbf = f0;
+    // per-function component scale sqrt((2L-1)!! / ((2l-1)!!(2m-1)!!(2n-1)!!))
+    for (const HostShell& s : b->shells)
+        for (int lx = s.l; lx >= 0; --lx)
+            for (int ly = s.l - lx; ly >= 0; --ly) {
+                const int lz = s.l - lx - ly;
+                b->fscale.push_back(sqrt(dfact(2 * s.l - 1) / (dfact(2 * lx - 1) * dfact(2 * ly - 1) * dfact(2 * lz - 1))));
+            }
+    return MESS_OK;
+}
+
+static mess_status build_pairs(mess_basis* b)
+{
+    const int ns = (int)b->shells.size();
+    std::vector<PrimPairRec<double>> pp64;
+    std::vector<PrimPairRec<float>> pp32;
+    std::vector<double> AB, Ccen;
+    std::vector<int> fa, fb, same;
+    const double kpref = sqrt(2.0) * pow(M_PI, 1.25);
+    for (int A = 0; A < ns; ++A) {
+        for (int B = 0; B < ns; ++B) {
+            const HostShell& sa = b->shells[A];
+            const HostShell& sb = b->shells[B];
+            const bool canonical = sa.l > sb.l || (sa.l == sb.l && A >= B);
+            if (!canonical) continue;
+            const int p = b->npair++;
+            b->pair_a.push_back(A);
+            b->pair_b.push_back(B);
+            b->pair_class.push_back(pclass_of(sa.l, sb.l));
+            b->pp_off.push_back((int)pp64.size());
+            double ab[3], ab2 = 0.0;
+            for (int x = 0; x < 3; ++x) {
+                ab[x] = sa.R[x] - sb.R[x];
+                ab2 += ab[x] * ab[x];
+                AB.push_back(ab[x]);
+                Ccen.push_back(sa.R[x]);
+            }
+            for (int i = 0; i < sa.K; ++i)
+                for (int j = 0; j < sb.K; ++j) {
+                    const double al = sa.alpha[i], be = sb.alpha[j], z = al + be;
+                    PrimPairRec<double> r{};
+                    r.v[0] = z;
+                    for (int x = 0; x < 3; ++x) {
+                        const double P = (al * sa.R[x] + be * sb.R[x]) / z;
+                        r.v[1 + x] = P;
+                        r.v[4 + x] = P - sa.R[x];
+                    }
+                    r.v[7] = kpref * sa.coef[i] * sb.coef[j] * exp(-al * be / z * ab2) / z;
+                    r.v[8] = 0.5 / z;
+                    pp64.push_back(r);
+                    PrimPairRec<float> f{};
+                    for (int k = 0; k < 12; ++k) f.v[k] = (float)r.v[k];
+                    pp32.push_back(f);
+                }
+            b->pp_n.push_back(sa.K * sb.K);
+            fa.push_back(sa.f0);
+            fb.push_back(sb.f0);
+            same.push_back(A == B ? 1 : 0);
+            (void)p;
+        }
+    }
+    MESS_CUDA_TRY(b->d_pp64.upload(pp64));
+    MESS_CUDA_TRY(b->d_pp32.upload(pp32));
+    MESS_CUDA_TRY(b->d_pp_off.upload(b->pp_off));
+    MESS_CUDA_TRY(b->d_pp_n.upload(b->pp_n));
+    MESS_CUDA_TRY(b->d_AB.upload(AB));
+    MESS_CUDA_TRY(b->d_Ccen.upload(Ccen));
+    MESS_CUDA_TRY(b->d_fa.upload(fa));
+    MESS_CUDA_TRY(b->d_fb.upload(fb));
+    MESS_CUDA_TRY(b->d_same.upload(same));
+    std::vector<double> tab;
+    mess_boys_table(tab);
+    MESS_CUDA_TRY(b->d_boys64.upload(tab));
+    std::vector<float> tab32(tab.begin(), tab.end());
+    MESS_CUDA_TRY(b->d_boys32.upload(tab32));
+    b->P64.pp = b->d_pp64.p;
+    b->P32.pp = b->d_pp32.p;
+    b->P64.pp_off = b->P32.pp_off = b->d_pp_off.p;
+    b->P64.pp_n = b->P32.pp_n = b->d_pp_n.p;
+    b->P64.AB = b->P32.AB = b->d_AB.p;
+    b->P64.fa = b->P32.fa = b->d_fa.p;
+    b->P64.fb = b->P32.fb = b->d_fb.p;
+    b->P64.same = b->P32.same = b->d_same.p;
+    b->P64.C = b->P32.C = b->d_Ccen.p;
+    b->P64.boys64 = b->P32.boys64 = b->d_boys64.p;
+    b->P64.boys32 = b->P32.boys32 = b->d_boys32.p;
+    // shells for the one-electron kernels
+    std::vector<int> sl, sK, sf0, spoff;
+    std::vector<double> sR, sal, sco;
+    for (const HostShell& s : b->shells) {
+        sl.push_back(s.l); sK.push_back(s.K); sf0.push_back(s.f0); spoff.push_back((int)sal.size());
+        for (int x = 0; x < 3; ++x) sR.push_back(s.R[x]);
+        sal.insert(sal.end(), s.alpha.begin(), s.alpha.end());
+        sco.insert(sco.end(), s.coef.begin(), s.coef.end());
+    }
+    MESS_CUDA_TRY(b->d_shell_l.upload(sl));
+    MESS_CUDA_TRY(b->d_shell_K.upload(sK));
+    MESS_CUDA_TRY(b->d_shell_f0.upload(sf0));
+    MESS_CUDA_TRY(b->d_shell_poff.upload(spoff));
+    MESS_CUDA_TRY(b->d_shell_R.upload(sR));
+    MESS_CUDA_TRY(b->d_shell_alpha.upload(sal));
+    MESS_CUDA_TRY(b->d_shell_coef.upload(sco));
+    MESS_CUDA_TRY(b->d_fscale.upload(b->fscale));
+    MESS_CUDA_TRY(b->d_pair_a.upload(b->pair_a));
+    MESS_CUDA_TRY(b->d_pair_b.upload(b->pair_b));
+    MESS_CUDA_TRY(b->d_Z.upload(b->Z));
+    MESS_CUDA_TRY(b->d_xyz.upload(b->xyz));
+    return MESS_OK;
+}
+
+static mess_status build_schwarz(mess_basis* b)
+{
+    std::vector<int> lists[MESS_NUM_PCLASS];
+    for (int p = 0; p < b->npair; ++p) lists[b->pair_class[p]].push_back(p);
+    MESS_CUDA_TRY(b->d_Q.alloc((size_t)std::max(1, b->npair)));
+    DevBuf<int> tmp[MESS_NUM_PCLASS];
+    for (int c = 0; c < MESS_NUM_PCLASS; ++c) {
+        if (lists[c].empty()) continue;
+        MESS_CUDA_TRY(tmp[c].upload(lists[c]));
+        ClassLaunchArgs a{};
+        a.kind = MESS_KIND_SCHWARZ;
+        a.pairs = tmp[c].p;
+        a.npairs = (int)lists[c].size();
+        a.P64_ptr = &b->P64;
+        a.P32_ptr = &b->P32;
+        a.out = b->d_Q.p;
+        a.stream = 0;
+        MESS_CUDA_TRY(MESS_CLASS_LAUNCHERS[qclass_of(c, c)](a));
+    }
+    MESS_CUDA_TRY(cudaDeviceSynchronize());
+    b->Q.resize(b->npair);
+    MESS_CUDA_TRY(cudaMemcpy(b->Q.data(), b->d_Q.p, sizeof(double) * b->npair, cudaMemcpyDeviceToHost));
+    for (int p = 0; p < b->npair; ++p)
+        if (!std::isfinite(b->Q[p])) { mess_set_error("non-finite Schwarz factor for pair %d", p); return MESS_ENUMERIC; }
+    for (int c = 0; c < MESS_NUM_PCLASS; ++c) {
+        std::vector<int> l = lists[c];
+        std::stable_sort(l.begin(), l.end(), [&](int x, int y) { return b->Q[x] > b->Q[y]; });
+        b->class_list[c] = l;
+        MESS_CUDA_TRY(b->d_class_list[c].upload(l));
+    }
+    return MESS_OK;
+}
+
+static void free_basis(mess_basis* b)
+{
+    b->d_pp64.free(); b->d_pp32.free(); b->d_pp_off.free(); b->d_pp_n.free(); b->d_fa.free();
+    b->d_fb.free(); b->d_same.free(); b->d_AB.free(); b->d_Ccen.free(); b->d_Q.free(); b->d_boys64.free();
+    b->d_boys32.free(); b->d_Z.free(); b->d_xyz.free(); b->d_shell_l.free(); b->d_shell_K.free();
+    b->d_shell_f0.free(); b->d_shell_poff.free(); b->d_shell_R.free(); b->d_shell_alpha.free();
+    b->d_shell_coef.free(); b->d_fscale.free(); b->d_pair_a.free(); b->d_pair_b.free();
+    for (auto& d : b->d_class_list) d.free();
+    b->bins.bra.free(); b->bins.kbeg.free(); b->bins.offs.free();
+}
+
+extern "C" mess_status mess_basis_create(int natom, const int* Z, const double* xyz_bohr, const char* basis_file,
+                                         mess_basis** out)
+{
+    if (!out) { mess_set_error("out is NULL"); return MESS_EINVAL; }
+    *out = nullptr;
+    if (natom <= 0 || !Z || !xyz_bohr || !basis_file) { mess_set_error("bad structure arguments"); return MESS_EINVAL; }
+    for (int i = 0; i < 3 * natom; ++i)
+        if (!std::isfinite(xyz_bohr[i])) { mess_set_error("non-finite coordinate"); return MESS_EINVAL; }
+    mess_basis* b = new (std::nothrow) mess_basis();
+    if (!b) { mess_set_error("host allocation failed"); return MESS_ENOMEM; }
+    b->natom = natom;
+    b->Z.assign(Z, Z + natom);
+    b->xyz.assign(xyz_bohr, xyz_bohr + 3 * natom);
+    mess_status st = build_basis(b, basis_file);
+    if (st == MESS_OK) st = build_pairs(b);
+    if (st == MESS_OK) st = build_schwarz(b);
+    if (st != MESS_OK) { free_basis(b); delete b; return st; }
+    *out = b;
+    return MESS_OK;
+}
+
+extern "C" int mess_basis_nbf(const mess_basis* b) { return b ? b->nbf : -1; }
+extern "C" int mess_basis_nshell(const mess_basis* b) { return b ? (int)b->shells.size() : -1; }
+extern "C" int mess_basis_nelectron(const mess_basis* b) { return b ? b->nelec : -1; }
+
+extern "C" void mess_basis_destroy(mess_basis* b)
+{
+    if (!b) return;
+    free_basis(b);
+    delete b;
+}
+
+extern "C" double mess_nuclear_repulsion(const mess_basis* b)
+{
+    if (!b) return NAN;
+    double e = 0.0;
+    for (int a = 0; a < b->natom; ++a)
+        for (int c = 0; c < a; ++c) {
+            double r2 = 0.0;
+            for (int x = 0; x < 3; ++x) { const double d = b->xyz[3 * a + x] - b->xyz[3 * c + x]; r2 += d * d; }
+            e += (double)b->Z[a] * b->Z[c] / sqrt(r2);
+        }
+    return e;
+}
+
+extern "C" mess_status mess_schwarz(const mess_basis* b, double* Q)
+{
+    if (!b || !Q) { mess_set_error("null argument"); return MESS_EINVAL; }
+    const int ns = (int)b->shells.size();
+    for (int i = 0; i < ns * ns; ++i) Q[i] = 0.0;
+    for (int p = 0; p < b->npair; ++p) {
+        Q[b->pair_a[p] * ns + b->pair_b[p]] = b->Q[p];
+        Q[b->pair_b[p] * ns + b->pair_a[p]] = b->Q[p];
+    }
+    return MESS_OK;
+}
+
+// ------------------------------------------------------------------------------------------ one-electron
+extern "C" mess_status mess_one_e_device(const mess_basis* b, double* dS, double* dT, double* dV, void* stream)
+{
+    if (!b) { mess_set_error("basis is NULL"); return MESS_EINVAL; }
+    MESS_CUDA_TRY(mess_launch_one_e(b, dS, dT, dV, (cudaStream_t)stream));
+    return MESS_OK;
+}
+
+static mess_status one_e_host(const mess_basis* b, double* S, double* T, double* V)
+{
+    if (!b) { mess_set_error("basis is NULL"); return MESS_EINVAL; }
+    const size_t nn = (size_t)b->nbf * b->nbf;
+    DevBuf<double> d;
+    MESS_CUDA_TRY(d.alloc(nn));
+    cudaError_t e = mess_launch_one_e(b, S ? d.p : nullptr, T ? d.p : nullptr, V ? d.p : nullptr, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(S ? S : (T ? T : V), d.p, nn * sizeof(double), cudaMemcpyDeviceToHost);
+    d.free();
+    if (e != cudaSuccess) { mess_set_error("one-electron integrals: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
+    return MESS_OK;
+}
+
+extern "C" mess_status mess_overlap(const mess_basis* b, double* S)
+{
+    if (!S) { mess_set_error("S is NULL"); return MESS_EINVAL; }
+    return one_e_host(b, S, nullptr, nullptr);
+}
+extern "C" mess_status mess_kinetic(const mess_basis* b, double* T)
+{
+    if (!T) { mess_set_error("T is NULL"); return MESS_EINVAL; }
+    return one_e_host(b, nullptr, T, nullptr);
+}
+extern "C" mess_status mess_nuclear(const mess_basis* b, double* V)
+{
+    if (!V) { mess_set_error("V is NULL"); return MESS_EINVAL; }
+    return one_e_host(b, nullptr, nullptr, V);
+}
+
+// ------------------------------------------------------------------------------------------ J / K
+// Algorithmic flops of one primitive quartet / one shell quartet of a class (FMA = 2 flops):
+// quartet set-up (exponent sums, P - Q, W - P, W - Q, T, prefactor) ~ 25, Boys (Taylor + exp +
+// downward recursion) 18 + 3L, prefactor scaling L + 1, the VRR op count, the contraction adds;
+// per shell quartet: the HRR op count and 6 FMAs per integral for the J/K digestion.
+static void class_flops(int qc, double* per_prim, double* per_shell)
+{
+    const mess_qclass_info& c = MESS_QCLASS[qc];
+    *per_prim = 25.0 + (18.0 + 3.0 * c.L) + (c.L + 1.0) + (double)c.vrr_flops + c.nacc;
+    *per_shell = (double)c.hrr_flops + 12.0 * c.nint;
+}
+
+static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
+                          mess_jk_info* info, mess_jk_part* parts, int max_parts, int* nparts)
+{
+    if (!b || !dD || !dJ || !dK) { mess_set_error("null argument"); return MESS_EINVAL; }
+    if (dD == dJ || dD == dK || dJ == dK) { mess_set_error("D, J and K must be distinct buffers"); return MESS_EINVAL; }
+    mess_jk_opts o{};
+    if (opts) o = *opts;
+    if (o.prec != MESS_FP64 && o.prec != MESS_MIXED && o.prec != MESS_FP32) {
+        mess_set_error("unknown precision %d", (int)o.prec);
+        return MESS_EINVAL;
+    }
+    if (!(o.schwarz_tau >= 0.0) || std::isnan(o.fp64_tau)) { mess_set_error("bad thresholds"); return MESS_EINVAL; }
+    double tau64 = o.fp64_tau == 0.0 ? MESS_DEFAULT_FP64_TAU : o.fp64_tau;
+    int split = 0;
+    if (o.prec == MESS_MIXED) split = tau64 > 0.0 ? 2 : 1;
+    else if (o.prec == MESS_FP32) split = 1;
+    if (split != 2) tau64 = 0.0;
+    mess_status st = mess_ensure_bins(b, o.schwarz_tau, tau64, split);
+    if (st != MESS_OK) return st;
+    if (parts && (int)b->bins.parts.size() > max_parts) {
+        mess_set_error("mess_jk_profile: %d launches, max_parts = %d", (int)b->bins.parts.size(), max_parts);
+        return MESS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)o.cuda_stream;
+    const int n = b->nbf;
+    const size_t bytes = (size_t)n * n * sizeof(double);
+    MESS_CUDA_TRY(cudaMemsetAsync(dJ, 0, bytes, s));
+    MESS_CUDA_TRY(cudaMemsetAsync(dK, 0, bytes, s));
+    std::vector<cudaEvent_t> ev;
+    if (parts) {
+        ev.resize(2 * b->bins.parts.size());
+        for (auto& e : ev) MESS_CUDA_TRY(cudaEventCreate(&e));
+    }
+    mess_jk_info inf{};
+    mess_status out = MESS_OK;
+    for (size_t k = 0; k < b->bins.parts.size(); ++k) {
+        const BinPart& p = b->bins.parts[k];
+        ClassLaunchArgs a{};
+        a.kind = MESS_KIND_JK;
+        a.mode = p.fp64 ? MESS_MODE_FP64 : (o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);
+        a.bin = bin_launch(b, p);
+        a.P64_ptr = &b->P64;
+        a.P32_ptr = &b->P32;
+        a.D = dD;
+        a.J = dJ;
+        a.K = dK;
+        a.n = n;
+        a.stream = s;
+        if (parts) cudaEventRecord(ev[2 * k], s);
+        cudaError_t e = MESS_CLASS_LAUNCHERS[p.qclass](a);
+        if (parts) cudaEventRecord(ev[2 * k + 1], s);
+        if (e != cudaSuccess) {
+            mess_set_error("J/K kernel launch (class %d): %s", p.qclass, cudaGetErrorString(e));
+            out = MESS_ECUDA;
+            break;
+        }
+        inf.shell_quartets += p.total;
+        inf.function_quartets += p.fn_quartets;
+        inf.primitive_quartets += p.prim_quartets;
+        if (p.fp64) inf.shell_quartets_fp64 += p.total;
+        inf.kernel_launches += 1;
+    }
+    if (out == MESS_OK) {
+        cudaError_t e = mess_launch_symmetrise_jk(dJ, dK, n, s);
+        if (e != cudaSuccess) { mess_set_error("symmetrise: %s", cudaGetErrorString(e)); out = MESS_ECUDA; }
+        inf.kernel_launches += 1;
+    }
+    if (parts && out == MESS_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { mess_set_error("profile sync: %s", cudaGetErrorString(e)); out = MESS_ECUDA; }
+        for (size_t k = 0; out == MESS_OK && k < b->bins.parts.size(); ++k) {
+            const BinPart& p = b->bins.parts[k];
+            const mess_qclass_info& c = MESS_QCLASS[p.qclass];
+            mess_jk_part& r = parts[k];
+            r.qclass = p.qclass;
+            r.la = c.la; r.lb = c.lb; r.lc = c.lc; r.ld = c.ld;
+            r.fp64 = p.fp64;
+            r.shell_quartets = p.total;
+            r.primitive_quartets = p.prim_quartets;
+            r.function_quartets = p.fn_quartets;
+            double fp, fs;
+            class_flops(p.qclass, &fp, &fs);
+            r.flops = fp * (double)p.prim_quartets + fs * (double)p.total;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+            r.ms = ms;
+        }
+        if (nparts) *nparts = (int)b->bins.parts.size();
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (info) *info = inf;
+    return out;
+}
+
+extern "C" mess_status mess_jk_build_device(const mess_basis* bc, const double* dD, double* dJ, double* dK,
+                                            const mess_jk_opts* opts, mess_jk_info* info)
+{
+    return jk_run(const_cast<mess_basis*>(bc), dD, dJ, dK, opts, info, nullptr, 0, nullptr);
+}
+
+extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, double* dJ, double* dK,
+                                       const mess_jk_opts* opts, mess_jk_part* parts, int max_parts, int* nparts)
+{
+    if (!parts || !nparts || max_parts <= 0) { mess_set_error("mess_jk_profile: no output array"); return MESS_EINVAL; }
+    return jk_run(const_cast<mess_basis*>(bc), dD, dJ, dK, opts, nullptr, parts, max_parts, nparts);
+}
+
+extern "C" mess_status mess_jk_build(const mess_basis* b, const double* D, double* J, double* K,
+                                     const mess_jk_opts* opts, mess_jk_info* info)
+{
+    if (!b || !D || !J || !K) { mess_set_error("null argument"); return MESS_EINVAL; }
+    const size_t nn = (size_t)b->nbf * b->nbf;
+    DevBuf<double> d;
+    MESS_CUDA_TRY(d.alloc(3 * nn));
+    mess_jk_opts o{};
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)o.cuda_stream;
+    mess_status st = MESS_OK;
+    cudaError_t e = cudaMemcpyAsync(d.p, D, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        st = mess_jk_build_device(b, d.p, d.p + nn, d.p + 2 * nn, &o, info);
+        if (st == MESS_OK) {
+            e = cudaMemcpyAsync(J, d.p + nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(K, d.p + 2 * nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+    }
+    d.free();
+    if (st != MESS_OK) return st;
+    if (e != cudaSuccess) { mess_set_error("jk_build: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
+    return MESS_OK;
+}
+
+extern "C" mess_status mess_eri_tensor(const mess_basis* bc, double* G)
+{
+    mess_basis* b = const_cast<mess_basis*>(bc);
+    if (!b || !G) { mess_set_error("null argument"); return MESS_EINVAL; }
+    const int n = b->nbf;
+    if (n > 64) { mess_set_error("mess_eri_tensor: n = %d > 64", n); return MESS_EINVAL; }
+    mess_status st = mess_ensure_bins(b, 0.0, 0.0, 0);
+    if (st != MESS_OK) return st;
+    const size_t n4 = (size_t)n * n * n * n;
+    DevBuf<double> d;
+    MESS_CUDA_TRY(d.alloc(n4));
+    cudaError_t e = cudaMemset(d.p, 0, n4 * sizeof(double));
+    for (const BinPart& p : b->bins.parts) {
+        if (e != cudaSuccess) break;
+        ClassLaunchArgs a{};
+        a.kind = MESS_KIND_STORE;
+        a.bin = bin_launch(b, p);
+        a.P64_ptr = &b->P64;
+        a.P32_ptr = &b->P32;
+        a.out = d.p;
+        a.n = n;
+        e = MESS_CLASS_LAUNCHERS[p.qclass](a);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(G, d.p, n4 * sizeof(double), cudaMemcpyDeviceToHost);
+    d.free();
+    if (e != cudaSuccess) { mess_set_error("eri_tensor: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
+    return MESS_OK;
+}

@@ -1,0 +1,29 @@
+// Plain-data layouts shared by the host code and the kernels (no torch types anywhere).
+#pragma once
+#include <stdint.h>
+
+// Boys-function grid: rows k = 0..MESS_BOYS_NROW-1 at T_k = k * MESS_BOYS_DT; columns n = 0..NF-1
+// hold F_n(T_k) and column NF holds exp(-T_k).
+#define MESS_BOYS_DT 0.1
+#define MESS_BOYS_INV_DT 10.0
+#define MESS_BOYS_TMAX64 36.0     // FP64 small-T branch below this (Taylor order 7)
+#define MESS_BOYS_TMAX32 30.0     // FP32 small-T branch below this (Taylor order 4)
+#define MESS_BOYS_NF 16
+#define MESS_BOYS_NCOL (MESS_BOYS_NF + 1)
+#define MESS_BOYS_NROW 362
+
+#define MESS_LMAX 2               // s, p, Cartesian d
+#define MESS_NUM_PCLASS 6         // pair classes (la,lb): ss ps pp ds dp dd
+
+// One primitive pair: zeta, Px, Py, Pz, PAx, PAy, PAz, K, 1/(2 zeta) (+ padding to 16 bytes).
+template <typename R> struct alignas(16) PrimPairRec { R v[12]; };
+
+// One launch over a class bin (a contiguous range of quartets of one angular class).
+struct BinLaunch {
+    const int* bra;          // [nbra] pair ids, Q descending
+    const int* ket;          // ket list (pair ids, Q descending)
+    const long long* offs;   // [nbra + 1] exclusive prefix of ket counts
+    const int* kbeg;         // [nbra] first ket index of each bra
+    int nbra;
+    long long total;
+};

@@ -21,3 +21,20 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+def build_library():
+    """Compile libmess.so (loads paper_2406_03121_gb300/build.py by path) and return its path."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2406_03121_gb300", "build.py")
+    spec = importlib.util.spec_from_file_location("_mess_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
+
+
+@pytest.fixture(scope="session")
+def mess():
+    build_library()
+    import paper_2406_03121_gb300 as m
+    return m

@@ -1,0 +1,167 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import mess_inputs as mi
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return [
+        ("h2o_sto3g", mi.h2o(), "sto-3g"),
+        ("h2o_631gs", mi.h2o(), "6-31gs"),
+        ("water2_631gs", mi.water_cluster(2, 9.0, 11), "6-31gs"),
+        ("propane_sto3g", mi.alkane(3, np.random.default_rng(21)), "sto-3g"),
+        ("ch4_631g", mi.alkane(1, np.random.default_rng(4)), "6-31g"),
+    ]
+
+
+CASES = _cases()
+IDS = [c[0] for c in CASES]
+
+
+def _pair(mess, oracle, mol, basis):
+    path = mi.basis_path(basis)
+    return mess.Basis.from_molecule(mol, path), oracle.basis_for(mol, path)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_one_electron_parity(mess, oracle_mod, case):
+    _, mol, basis = case
+    g, o = _pair(mess, oracle_mod, mol, basis)
+    assert g.nbf == o.nfn
+    S, T, V = oracle_mod.one_e(o)
+    assert np.abs(g.overlap() - S).max() < 1e-12
+    assert np.abs(g.kinetic() - T).max() < 1e-11
+    assert np.abs(g.nuclear() - V).max() < 1e-11
+    assert g.nuclear_repulsion() == pytest.approx(oracle_mod.nuclear_repulsion(mol.Z, mol.xyz), rel=1e-15)
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[4]], ids=[IDS[0], IDS[1], IDS[4]])
+def test_eri_tensor_parity_every_class(mess, oracle_mod, case):
+    """Every integral of the basis (s, p, Cartesian d: all 21 shell-quartet classes for 6-31G*)."""
+    _, mol, basis = case
+    g, o = _pair(mess, oracle_mod, mol, basis)
+    G = g.eri_tensor()
+    ref = oracle_mod.eri_tensor(o)
+    assert np.abs(G - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_schwarz_parity(mess, oracle_mod, case):
+    _, mol, basis = case
+    g, o = _pair(mess, oracle_mod, mol, basis)
+    assert np.abs(g.schwarz() - oracle_mod.schwarz(o)).max() < 1e-12
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_jk_fp64_parity(mess, oracle_mod, case):
+    _, mol, basis = case
+    g, o = _pair(mess, oracle_mod, mol, basis)
+    D = mi.random_symmetric_density(g.nbf, 17)
+    J, K, info = g.jk(D, prec="fp64")
+    Jr, Kr = oracle_mod.jk(o, D)
+    assert np.abs(J - Jr).max() <= 1e-8
+    assert np.abs(K - Kr).max() <= 1e-8
+    n = g.nbf
+    assert info["function_quartets"] == (n * (n + 1) // 2) * (n * (n + 1) // 2 + 1) // 2
+
+
+def test_jk_screened_parity(mess, oracle_mod):
+    mol = mi.water_cluster(4, 18.0, 5)
+    g, o = _pair(mess, oracle_mod, mol, "sto-3g")
+    D = mi.random_symmetric_density(g.nbf, 23)
+    Q = oracle_mod.schwarz(o)
+    for tau in (1e-10, 1e-6):
+        J, K, info = g.jk(D, prec="fp64", schwarz_tau=tau)
+        Jr, Kr = oracle_mod.jk(o, D, tau=tau, Q=Q)
+        assert np.abs(J - Jr).max() <= 1e-8
+        assert np.abs(K - Kr).max() <= 1e-8
+    full = g.jk(D, prec="fp64")[2]
+    assert info["shell_quartets"] < full["shell_quartets"]
+
+
+def _two_electron_energy(D, J, K):
+    return 0.5 * float(np.sum(D * (J - 0.5 * K)))
+
+
+@pytest.fixture(scope="module")
+def water2_scf(oracle_mod):
+    mol = mi.water_cluster(2, 9.0, 11)
+    o = oracle_mod.basis_for(mol, mi.basis_path("6-31gs"))
+    r = oracle_mod.scf(o)
+    assert r.converged
+    J, K = oracle_mod.jk(o, r.D)
+    return mol, r.D, J, K
+
+
+@pytest.mark.parametrize("prec,fp64_tau,boys64,tol", [
+    ("mixed", 0.0, False, 1e-6),     # default split (Q_ab Q_cd >= 3e-2 in FP64): the reduced-precision bar
+    ("mixed", 1e-3, True, 1e-6),
+    ("mixed", -1.0, False, 2e-5),    # no FP64 quartets at all: reported, not held to the bar
+    ("fp32", 0.0, False, 2e-5),
+])
+def test_jk_reduced_precision_energy(mess, water2_scf, prec, fp64_tau, boys64, tol):
+    mol, D, Jr, Kr = water2_scf
+    g = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
+    J, K, info = g.jk(D, prec=prec, fp64_tau=fp64_tau, boys_fp64=boys64)
+    dE = abs(_two_electron_energy(D, J, K) - _two_electron_energy(D, Jr, Kr))
+    assert dE <= tol, dE
+    assert np.abs(J - Jr).max() < 1e-4 and np.abs(K - Kr).max() < 1e-4
+    if prec == "mixed" and fp64_tau >= 0:
+        assert 0 < info["shell_quartets_fp64"] < info["shell_quartets"]
+    else:
+        assert info["shell_quartets_fp64"] == 0
+
+
+def test_jk_device_matches_host(mess):
+    import torch
+    mol = mi.water_cluster(2, 9.0, 11)
+    g = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
+    D = mi.random_symmetric_density(g.nbf, 3)
+    J, K, _ = g.jk(D)
+    dD = torch.from_numpy(D).cuda()
+    dJ = torch.empty_like(dD)
+    dK = torch.empty_like(dD)
+    s = torch.cuda.current_stream()
+    g.jk_device(dD, dJ, dK, stream=s)
+    torch.cuda.synchronize()
+    assert np.abs(dJ.cpu().numpy() - J).max() == 0.0 or np.abs(dJ.cpu().numpy() - J).max() < 1e-12
+    assert np.abs(dK.cpu().numpy() - K).max() < 1e-12
+
+
+def test_full_size_water8_sampled(mess, oracle_mod):
+    """(H2O)_8 / 6-31G* (152 functions) at tau = 1e-10: sampled J/K elements against the oracle."""
+    mol = mi.water_cluster(8, 12.0, 2002)
+    g, o = _pair(mess, oracle_mod, mol, "6-31gs")
+    assert g.nbf == 152
+    D = mi.random_symmetric_density(g.nbf, 2002)
+    Q = oracle_mod.schwarz(o)
+    rng = np.random.default_rng(0)
+    rows = rng.integers(0, g.nbf, 12)
+    cols = rng.integers(0, g.nbf, 12)
+    Jr, Kr = oracle_mod.jk_elements(o, D, rows, cols, tau=1e-10, Q=Q)
+    for prec, tol in (("fp64", 1e-8), ("mixed", 2e-5)):
+        J, K, info = g.jk(D, prec=prec, schwarz_tau=1e-10)
+        assert np.abs(J[rows, cols] - Jr).max() <= tol
+        assert np.abs(K[rows, cols] - Kr).max() <= tol
+        assert np.allclose(J, J.T) and np.allclose(K, K.T)
+
+
+def test_single_atom_and_errors(mess, oracle_mod, tmp_path):
+    he = mi.Molecule("he", np.array([2], dtype=np.int32), np.zeros((1, 3)))
+    g, o = _pair(mess, oracle_mod, he, "sto-3g")
+    D = np.array([[1.7]])
+    J, K, info = g.jk(D)
+    ref = oracle_mod.eri(o, 0, 0, 0, 0) * 1.7
+    assert J[0, 0] == pytest.approx(ref, rel=1e-13) and K[0, 0] == pytest.approx(ref, rel=1e-13)
+    assert info["shell_quartets"] == 1
+    with pytest.raises(mess.MessError):
+        mess.Basis([11], [[0, 0, 0]], mi.basis_path("sto-3g"))
+    with pytest.raises(mess.MessError):
+        mess.Basis([1], [[0, 0, 0]], str(tmp_path / "missing.basis"))
+    bad = tmp_path / "bad.basis"
+    bad.write_text("element H\nS 2\n 1.0 1.0\n")
+    with pytest.raises(mess.MessError):
+        mess.Basis([1], [[0, 0, 0]], str(bad))
