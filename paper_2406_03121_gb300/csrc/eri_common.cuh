@@ -184,6 +184,14 @@ struct DigestCtx {
     bool warp_reduce_ab;   // all 32 lanes share the bra pair: reduce J_ab across the warp first
 };
 
+// sum over aligned groups of G consecutive lanes (G a power of two); every lane of the warp takes part
+template <int G, typename R> __device__ __forceinline__ R group_sum(R v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <typename R> __device__ __forceinline__ R warp_sum(R v)
 {
 #pragma unroll
@@ -225,21 +233,23 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
 
 #define MESS_THREADS 128
 
-// JK kernel of one class: one thread per shell quartet of the bin.
+// JK kernel of one class: G consecutive lanes per shell quartet of the bin (G = 1: one thread).
 #define MESS_DEFINE_CLASS_KERNELS(TAG, NA, NB, NC, ND)                                             \
-    template <typename R, int BMODE>                                                                \
+    template <typename R, int BMODE, int G>                                                         \
     __global__ void __launch_bounds__(MESS_THREADS)                                                 \
     k_jk_##TAG(const BinLaunch b, const PairTable<R> P, const double* __restrict__ D,               \
                double* __restrict__ J, double* __restrict__ K, int n)                               \
     {                                                                                               \
-        const long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;                     \
+        const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;                     \
+        const long long q0 = t0 / G;                                                                \
+        const int g = (int)(t0 % G);                                                                \
         const bool valid = q0 < b.total;                                                            \
         const long long q = valid ? q0 : b.total - 1;                                               \
         const int i = find_bra(b.offs, b.nbra, q);                                                  \
         const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));                            \
         const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);                                     \
         R I[(NA) * (NB) * (NC) * (ND)];                                                             \
-        eri_##TAG<R, BMODE>(P, bp, kp, I);                                                          \
+        eri_##TAG<R, BMODE, G>(P, bp, kp, g, I);                                                    \
         DigestCtx c;                                                                                \
         c.D = D; c.J = J; c.K = K; c.n = n;                                                         \
         c.fa = __ldg(P.fa + bp); c.fb = __ldg(P.fb + bp);                                           \
@@ -248,8 +258,13 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         if (__ldg(P.same + bp)) s *= R(0.5);                                                        \
         if (__ldg(P.same + kp)) s *= R(0.5);                                                        \
         if (bp == kp) s *= R(0.5);                                                                  \
-        c.warp_reduce_ab = warp_uniform_int(bp);                                                    \
-        digest_##TAG<R>(I, c, s);                                                                   \
+        if (G == 1) {                                                                               \
+            c.warp_reduce_ab = warp_uniform_int(bp);                                                \
+            digest_##TAG<R>(I, c, s);                                                               \
+        } else if (g == 0) {                                                                        \
+            c.warp_reduce_ab = false;                                                               \
+            digest_##TAG<R>(I, c, s);                                                               \
+        }                                                                                           \
     }                                                                                               \
     /* every integral of the bin written to a dense n^4 tensor, all 8 index permutations */         \
     __global__ void __launch_bounds__(MESS_THREADS)                                                 \
@@ -261,7 +276,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         const int j = b.kbeg[i] + (int)(q - b.offs[i]);                                             \
         const int bp = b.bra[i], kp = b.ket[j];                                                     \
         double I[(NA) * (NB) * (NC) * (ND)];                                                        \
-        eri_##TAG<double, 0>(P, bp, kp, I);                                                         \
+        eri_##TAG<double, 0, 1>(P, bp, kp, 0, I);                                                   \
         const int fa = P.fa[bp], fb = P.fb[bp], fc = P.fa[kp], fd = P.fb[kp];                       \
         const size_t nn = (size_t)n;                                                                \
         for (int ia = 0; ia < (NA); ++ia)                                                           \
@@ -291,7 +306,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         if (t >= npairs) return;                                                                    \
         const int p = pairs[t];                                                                     \
         double I[(NA) * (NB) * (NA) * (NB)];                                                        \
-        eri_##TAG<double, 0>(P, p, p, I);                                                           \
+        eri_##TAG<double, 0, 1>(P, p, p, 0, I);                                                     \
         double m = 0.0;                                                                             \
         for (int ia = 0; ia < (NA); ++ia)                                                           \
             for (int ib = 0; ib < (NB); ++ib)                                                       \
@@ -389,4 +404,173 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
     }
 #pragma unroll 1
     for (int k = 0; k < NINT; ++k) I[k] = R(__ldg(fscale + k)) * H[__ldg(fslot + k)];
+}
+
+
+// ------------------------------------------------------------------------------------------
+// Warp-per-quartet J/K kernel for the large classes: the 32 lanes of a warp run the independent
+// ops of one dependency level of the level-scheduled program in parallel (values in shared
+// memory, __syncwarp between levels), then split the digestion outputs between them.
+// ------------------------------------------------------------------------------------------
+
+template <typename R, int BMODE, int L, int NVI, int NH, int NACC, int NVL, int NHL, int NINT,
+          int NA, int NB, int NC, int ND>
+__device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable<R>& P, const double* __restrict__ D,
+                                             double* __restrict__ J, double* __restrict__ K, int n,
+                                             const uint4* __restrict__ vprog, const int* __restrict__ vlev,
+                                             const uint2* __restrict__ hprog, const int* __restrict__ hlev,
+                                             const int* __restrict__ fslot, const double* __restrict__ fscale,
+                                             R* __restrict__ sm)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long q = (long long)blockIdx.x * MESS_TEAM_WARPS + warp;
+    if (q >= b.total) return;                       // whole warp leaves together
+    R* V = sm + (size_t)warp * (NVI + NH);
+    R* H = V + NVI;
+    const int i = find_bra(b.offs, b.nbra, q);
+    const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));
+    const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);
+    for (int k = lane; k < NACC; k += 32) H[k] = R(0);
+    __syncwarp();
+    const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];
+    const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
+    const R ACx = R(P.C[3 * bp] - P.C[3 * kp]), ACy = R(P.C[3 * bp + 1] - P.C[3 * kp + 1]);
+    const R ACz = R(P.C[3 * bp + 2] - P.C[3 * kp + 2]);
+#pragma unroll 1
+    for (int ib = b0; ib < b1; ++ib) {
+        const PrimPair<R> pb = P.load(ib);
+#pragma unroll 1
+        for (int ik = k0; ik < k1; ++ik) {
+            const PrimPair<R> pk = P.load(ik);
+            const R rz = R(1) / (pb.zeta + pk.zeta);
+            const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;
+            const R PQx = pb.PAx - pk.PAx + ACx, PQy = pb.PAy - pk.PAy + ACy, PQz = pb.PAz - pk.PAz + ACz;
+            const R WPx = -roz * PQx, WPy = -roz * PQy, WPz = -roz * PQz;
+            const R WQx = roe * PQx, WQy = roe * PQy, WQz = roe * PQz;
+            const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);
+            const R pref = pb.K * pk.K * prefactor_sqrt(rz);
+            R F[L + 1];
+            boys_eval<R, L, BMODE>(T, F, P.boys64, P.boys32);
+#pragma unroll
+            for (int m = 0; m <= L; ++m) F[m] *= pref;
+#pragma unroll 1
+            for (int lv = 0; lv < NVL; ++lv) {
+                const int oend = __ldg(vlev + lv + 1);
+#pragma unroll 1
+                for (int o = __ldg(vlev + lv) + lane; o < oend; o += 32) {
+                    const uint4 w = __ldg(vprog + o);
+                    const int kind = w.x & 3, d = (w.x >> 2) & 3;
+                    const int m1 = (w.x >> 4) & 15, m2 = (w.x >> 8) & 15, t = w.x >> 16;
+                    const int s1 = w.y & 0xffff, s2 = w.y >> 16;
+                    if (kind == 0) {
+                        R f = F[0];
+#pragma unroll
+                        for (int m = 1; m <= L; ++m) f = (s1 == m) ? F[m] : f;
+                        V[t] = f;
+                    } else if (kind == 3) {
+                        H[s1] += V[t];
+                    } else if (kind == 1) {
+                        R v = pick3(d, pb.PAx, pb.PAy, pb.PAz) * V[s1] + pick3(d, WPx, WPy, WPz) * V[s2];
+                        if (m1) v += R(m1) * pb.oo2z * (V[w.z & 0xffff] - roz * V[w.z >> 16]);
+                        V[t] = v;
+                    } else {
+                        R v = pick3(d, pk.PAx, pk.PAy, pk.PAz) * V[s1] + pick3(d, WQx, WQy, WQz) * V[s2];
+                        if (m1) v += R(m1) * pk.oo2z * (V[w.z & 0xffff] - roe * V[w.z >> 16]);
+                        if (m2) v += R(m2) * oo2ze * V[w.w];
+                        V[t] = v;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+    const R ABx = R(P.AB[3 * bp]), ABy = R(P.AB[3 * bp + 1]), ABz = R(P.AB[3 * bp + 2]);
+    const R CDx = R(P.AB[3 * kp]), CDy = R(P.AB[3 * kp + 1]), CDz = R(P.AB[3 * kp + 2]);
+#pragma unroll 1
+    for (int lv = 0; lv < NHL; ++lv) {
+        const int oend = __ldg(hlev + lv + 1);
+#pragma unroll 1
+        for (int o = __ldg(hlev + lv) + lane; o < oend; o += 32) {
+            const uint2 w = __ldg(hprog + o);
+            const int t = w.x & 0xffff, d = (w.x >> 16) & 3, side = (w.x >> 18) & 1;
+            const R X = side ? pick3(d, CDx, CDy, CDz) : pick3(d, ABx, ABy, ABz);
+            H[t] = H[w.y & 0xffff] + X * H[w.y >> 16];
+        }
+        __syncwarp();
+    }
+    for (int k = lane; k < NINT; k += 32) V[k] = R(__ldg(fscale + k)) * H[__ldg(fslot + k)];
+    __syncwarp();
+    const R* I = V;
+    R s = R(1);
+    if (__ldg(P.same + bp)) s *= R(0.5);
+    if (__ldg(P.same + kp)) s *= R(0.5);
+    if (bp == kp) s *= R(0.5);
+    const int fa = __ldg(P.fa + bp), fb = __ldg(P.fb + bp), fc = __ldg(P.fa + kp), fd = __ldg(P.fb + kp);
+    const size_t nn = (size_t)n;
+#define MESS_I(a_, b_, c_, d_) I[(((a_) * NB + (b_)) * NC + (c_)) * ND + (d_)]
+    for (int o = lane; o < NA * NB; o += 32) {          // J_ab = sum_cd I D_cd
+        const int a = o / NB, bb = o % NB;
+        R t = R(0);
+        for (int c = 0; c < NC; ++c)
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fc + c) * nn + fd + d));
+        atomicAdd(J + (fa + a) * nn + fb + bb, (double)(s * t));
+    }
+    for (int o = lane; o < NC * ND; o += 32) {          // J_cd = sum_ab I D_ab
+        const int c = o / ND, d = o % ND;
+        R t = R(0);
+        for (int a = 0; a < NA; ++a)
+            for (int bb = 0; bb < NB; ++bb) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fa + a) * nn + fb + bb));
+        atomicAdd(J + (fc + c) * nn + fd + d, (double)(s * t));
+    }
+    for (int o = lane; o < NA * NC; o += 32) {          // K_ac = sum_bd I D_bd
+        const int a = o / NC, c = o % NC;
+        R t = R(0);
+        for (int bb = 0; bb < NB; ++bb)
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fb + bb) * nn + fd + d));
+        atomicAdd(K + (fa + a) * nn + fc + c, (double)(s * t));
+    }
+    for (int o = lane; o < NA * ND; o += 32) {          // K_ad = sum_bc I D_bc
+        const int a = o / ND, d = o % ND;
+        R t = R(0);
+        for (int bb = 0; bb < NB; ++bb)
+            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fb + bb) * nn + fc + c));
+        atomicAdd(K + (fa + a) * nn + fd + d, (double)(s * t));
+    }
+    for (int o = lane; o < NB * NC; o += 32) {          // K_bc = sum_ad I D_ad
+        const int bb = o / NC, c = o % NC;
+        R t = R(0);
+        for (int a = 0; a < NA; ++a)
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fa + a) * nn + fd + d));
+        atomicAdd(K + (fb + bb) * nn + fc + c, (double)(s * t));
+    }
+    for (int o = lane; o < NB * ND; o += 32) {          // K_bd = sum_ac I D_ac
+        const int bb = o / ND, d = o % ND;
+        R t = R(0);
+        for (int a = 0; a < NA; ++a)
+            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fa + a) * nn + fc + c));
+        atomicAdd(K + (fb + bb) * nn + fd + d, (double)(s * t));
+    }
+#undef MESS_I
+}
+
+#define MESS_DEFINE_TEAM_KERNEL_IMPL(TAG, ...)                                                      \
+    template <typename R> constexpr size_t team_smem_##TAG()                                        \
+    {                                                                                               \
+        return team_smem_bytes<R, __VA_ARGS__>();                                                   \
+    }                                                                                               \
+    template <typename R, int BMODE>                                                                \
+    __global__ void __launch_bounds__(32 * MESS_TEAM_WARPS)                                         \
+    k_jk_team_##TAG(const BinLaunch b, const PairTable<R> P, const double* __restrict__ D,          \
+                    double* __restrict__ J, double* __restrict__ K, int n)                          \
+    {                                                                                               \
+        extern __shared__ __align__(16) unsigned char mess_team_smem[];                             \
+        jk_team_body<R, BMODE, __VA_ARGS__>(b, P, D, J, K, n, MESS_TEAM_PROG_##TAG,                 \
+                                            reinterpret_cast<R*>(mess_team_smem));                  \
+    }
+#define MESS_DEFINE_TEAM_KERNEL(TAG) MESS_DEFINE_TEAM_KERNEL_IMPL(TAG, MESS_TEAM_ARGS_##TAG)
+
+template <typename R, int L, int NVI, int NH, int NACC, int NVL, int NHL, int NINT, int NA, int NB, int NC, int ND>
+constexpr size_t team_smem_bytes()
+{
+    return (size_t)MESS_TEAM_WARPS * (NVI + NH) * sizeof(R);
 }

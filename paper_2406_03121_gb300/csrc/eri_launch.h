@@ -14,6 +14,7 @@ enum { MESS_MODE_FP64 = 0, MESS_MODE_MIXED = 1, MESS_MODE_FP32 = 2 };
 struct ClassLaunchArgs {
     int kind;                    // MESS_KIND_*
     int mode;                    // MESS_MODE_* (JK only)
+    int G;                       // JK: lanes per shell quartet (1 or 8)
     BinLaunch bin;               // JK / STORE
     const int* pairs;            // SCHWARZ: pair ids of one diagonal class
     int npairs;
@@ -29,3 +30,22 @@ struct ClassLaunchArgs {
 
 typedef cudaError_t (*mess_class_launcher)(const ClassLaunchArgs&);
 extern const mess_class_launcher MESS_CLASS_LAUNCHERS[MESS_NUM_QCLASS];
+
+// Launch of a warp-per-quartet kernel with its dynamic shared memory (opt-in above 48 KB, set
+// once per kernel).
+template <typename R, int BMODE, typename Kern>
+cudaError_t mess_team_launch(Kern kern, dim3 grid, size_t smem, const ClassLaunchArgs& a, const PairTable<R>& P,
+                             int* configured /* per kernel: 0 until the attribute is set on this device */)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = 1;
+    }
+    kern<<<grid, 32 * MESS_TEAM_WARPS, smem, a.stream>>>(a.bin, P, a.D, a.J, a.K, a.n);
+    return cudaGetLastError();
+}

@@ -379,6 +379,163 @@ def build_program(cls):
                 na=ncart(la), nb=ncart(lb), nc=ncart(lc), nd=ncart(ld))
 
 
+def _level_alloc(values, deflev, lastlev, pinned_slots=None, pinned_end=()):
+    """Slots for level-parallel execution: a value occupies its slot from its defining level
+    through its last-use level; a slot is reused only by a value defined at a later level."""
+    for v in pinned_end:
+        lastlev[v] = 10 ** 9
+    slot = dict(pinned_slots or {})
+    nslots = max(slot.values()) + 1 if slot else 0
+    busy_until = {sl: lastlev[v] for v, sl in slot.items()}   # slot -> last level it is read
+    order = sorted((v for v in values if v not in slot), key=lambda v: deflev[v])
+    free = []
+    for v in order:
+        L = deflev[v]
+        # release slots whose occupant was last read before level L
+        for sl, until in list(busy_until.items()):
+            if until < L:
+                free.append(sl)
+                del busy_until[sl]
+        if free:
+            free.sort()
+            sl = free.pop(0)
+        else:
+            sl = nslots
+            nslots += 1
+        slot[v] = sl
+        busy_until[sl] = lastlev.get(v, L)
+    return slot, nslots
+
+
+def build_team_program(cls):
+    """Level-scheduled op program for one warp per shell quartet (lanes run the independent ops of
+    one dependency level in parallel; values in shared memory)."""
+    (la, lb), (lc, ld) = cls
+    v = VRR(la, lb, lc, ld)
+    nf = len(v.fs)
+    accidx = {}
+    for ei, e in enumerate(v.es):
+        for fi, f in enumerate(v.fs):
+            accidx[(e, f, 0)] = ei * nf + fi
+    lev, deps = {}, {}
+    meta = {}
+    for key in v.order:
+        e, f, m = key
+        if sum(e) == 0 and sum(f) == 0:
+            d, info = [], (0, [], m, 0, 0, 0)
+        elif sum(f) > 0:
+            i = pick_dir(f)
+            f1 = sub(f, i)
+            srcs = [(e, f1, m), (e, f1, m + 1)]
+            m1 = f1[i]
+            srcs += [(e, sub(f1, i), m), (e, sub(f1, i), m + 1)] if m1 >= 1 else [None, None]
+            m2 = e[i]
+            srcs += [(sub(e, i), f1, m + 1)] if m2 >= 1 else [None]
+            d, info = [x for x in srcs if x is not None], (2, srcs, None, i, m1, m2)
+        else:
+            i = pick_dir(e)
+            e1 = sub(e, i)
+            srcs = [(e1, f, m), (e1, f, m + 1)]
+            m1 = e1[i]
+            srcs += [(sub(e1, i), f, m), (sub(e1, i), f, m + 1)] if m1 >= 1 else [None, None]
+            srcs += [None]
+            d, info = [x for x in srcs if x is not None], (1, srcs, None, i, m1, 0)
+        lev[key] = 1 + max([lev[x] for x in d], default=-1)
+        deps[key] = d
+        meta[key] = info
+    # ACC ops one level after their value
+    lastv = {}
+    for key in v.order:
+        for x in deps[key]:
+            lastv[x] = max(lastv.get(x, -1), lev[key])
+    for key in accidx:
+        lastv[key] = max(lastv.get(key, -1), lev[key] + 1)
+    vslot, nv = _level_alloc(list(v.order), lev, lastv)
+    nlev = max(lev.values()) + 2
+    ops_by_level = [[] for _ in range(nlev)]
+    for key in v.order:
+        kind, srcs, m, d, m1, m2 = meta[key]
+        if kind == 0:
+            ops_by_level[lev[key]].append((0, vslot[key], m, 0, 0, 0, 0, 0, 0, 0))
+        else:
+            ss = [vslot[x] if x is not None else 0 for x in srcs]
+            ops_by_level[lev[key]].append((kind, vslot[key], ss[0], ss[1], ss[2], ss[3], ss[4], d, m1, m2))
+    for key, k in accidx.items():
+        ops_by_level[lev[key] + 1].append((3, vslot[key], k, 0, 0, 0, 0, 0, 0, 0))
+    ops_by_level = [l for l in ops_by_level if l]
+    vops, vlev = [], [0]
+    for l in ops_by_level:
+        vops += l
+        vlev.append(len(vops))
+    # HRR: same value graph as build_program, scheduled by levels
+    eidx = {e: k for k, e in enumerate(v.es)}
+    fidx = {f: k for k, f in enumerate(v.fs)}
+    hops, hlevel = [], {}
+    memo_b, memo_k = {}, {}
+
+    def gb(a, b, fi):
+        key = ("b", a, b, fi)
+        if key in memo_b:
+            return memo_b[key]
+        if sum(b) == 0:
+            val = ("acc", eidx[a] * nf + fi)
+            hlevel[val] = 0
+        else:
+            i = pick_dir(b)
+            b1 = sub(b, i)
+            t1, t2 = gb(add(a, i), b1, fi), gb(a, b1, fi)
+            val = key
+            hlevel[val] = 1 + max(hlevel[t1], hlevel[t2])
+            hops.append((val, t1, t2, i, 0))
+        memo_b[key] = val
+        return val
+
+    def gk(a, b, c, dd):
+        key = ("k", a, b, c, dd)
+        if key in memo_k:
+            return memo_k[key]
+        if sum(dd) == 0:
+            val = gb(a, b, fidx[c])
+        else:
+            i = pick_dir(dd)
+            d1 = sub(dd, i)
+            t1, t2 = gk(a, b, add(c, i), d1), gk(a, b, c, d1)
+            val = key
+            hlevel[val] = 1 + max(hlevel[t1], hlevel[t2])
+            hops.append((val, t1, t2, i, 1))
+        memo_k[key] = val
+        return val
+    finals = []
+    for a in cart(la):
+        for b in cart(lb):
+            for c in cart(lc):
+                for dd in cart(ld):
+                    finals.append((gk(a, b, c, dd), comp_scale(a) * comp_scale(b) * comp_scale(c) * comp_scale(dd)))
+    nacc = len(v.es) * nf
+    lasth = {}
+    for (t, s1, s2, d, side) in hops:
+        for x in (s1, s2):
+            lasth[x] = max(lasth.get(x, 0), hlevel[t])
+    for k in range(nacc):
+        lasth.setdefault(("acc", k), 0)
+    pinned = {("acc", k): k for k in range(nacc)}
+    values = [h[0] for h in hops]
+    hslot, nh = _level_alloc(values, hlevel, lasth, pinned, pinned_end=[f for f, _ in finals])
+    nhl = max([hlevel[h[0]] for h in hops], default=0)
+    hops_by_level = [[] for _ in range(nhl + 1)]
+    for (t, s1, s2, d, side) in hops:
+        hops_by_level[hlevel[t]].append((hslot[t], hslot[s1], hslot[s2], d, side))
+    hops_by_level = [l for l in hops_by_level if l]
+    hprog, hlev = [], [0]
+    for l in hops_by_level:
+        hprog += l
+        hlev.append(len(hprog))
+    fin = [(hslot[f], sc) for f, sc in finals]
+    nint = len(fin)
+    return dict(vrr=vops, vlev=vlev, nv=nv, hrr=hprog, hlev=hlev, nh=nh, fin=fin, nacc=nacc,
+                L=la + lb + lc + ld, nint=nint, na=ncart(la), nb=ncart(lb), nc=ncart(lc), nd=ncart(ld))
+
+
 def straight_line(info):
     """classes emitted as straight-line register code (the rest run the op-program kernel)"""
     return info["nacc"] <= 96 and info["nvrr"] <= 280
@@ -399,47 +556,65 @@ def emit_class_straight(cls):
     nacc = len(v.es) * len(v.fs)
     lines = []
     lines.append(f"// ---- class ({la}{lb}|{lc}{ld}): {len(v.order)} VRR entries, {nacc} contracted, {nint} integrals")
-    lines.append(f"template <typename R, int BMODE>")
-    lines.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, R* I)")
+    lines.append(f"template <typename R, int BMODE, int G>")
+    lines.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I)")
     lines.append("{")
     lines.append(f"    R acc[{nacc}];")
     lines.append(f"#pragma unroll")
     lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = R(0);")
     lines.append("    const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];")
-    lines.append("    const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];")
+    lines.append("    const int k0 = P.pp_off[kp], nk = P.pp_n[kp], k1 = k0 + nk;")
     lines.append("    // A - C in FP64, then P - Q = (P - A) - (Q - C) + (A - C): no absolute coordinates in R")
     lines.append("    const R ACx = R(P.C[3 * bp] - P.C[3 * kp]), ACy = R(P.C[3 * bp + 1] - P.C[3 * kp + 1]);")
     lines.append("    const R ACz = R(P.C[3 * bp + 2] - P.C[3 * kp + 2]);")
+    body = []
+    body.append("            const R rz = R(1) / (pb.zeta + pk.zeta);")
+    body.append("            const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;")
+    body.append("            const R oo2z = pb.oo2z, oo2e = pk.oo2z;")
+    body.append("            (void)roe; (void)roz; (void)oo2ze; (void)oo2z; (void)oo2e;")
+    body.append("            const R PQx = pb.PAx - pk.PAx + ACx, PQy = pb.PAy - pk.PAy + ACy, PQz = pb.PAz - pk.PAz + ACz;")
+    body.append("            const R PAx = pb.PAx, PAy = pb.PAy, PAz = pb.PAz;")
+    body.append("            const R QCx = pk.PAx, QCy = pk.PAy, QCz = pk.PAz;")
+    body.append("            const R WPx = -roz * PQx, WPy = -roz * PQy, WPz = -roz * PQz;")
+    body.append("            const R WQx = roe * PQx, WQy = roe * PQy, WQz = roe * PQz;")
+    body.append("            (void)PAx; (void)PAy; (void)PAz; (void)QCx; (void)QCy; (void)QCz;")
+    body.append("            (void)WPx; (void)WPy; (void)WPz; (void)WQx; (void)WQy; (void)WQz;")
+    body.append("            const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);")
+    body.append("            const R pref = pb.K * pk.K * prefactor_sqrt(rz);")
+    body.append(f"            R F[{L + 1}];")
+    body.append(f"            boys_eval<R, {L}, BMODE>(T, F, P.boys64, P.boys32);")
+    body.append("#pragma unroll")
+    body.append(f"            for (int m = 0; m <= {L}; ++m) F[m] *= pref;")
+    vflops = v.emit(body, "            ")
+    for ei, e in enumerate(v.es):
+        for fi, f in enumerate(v.fs):
+            body.append(f"            acc[{ei * len(v.fs) + fi}] += {v.names[(e, f, 0)]};")
+    lines.append("    if constexpr (G == 1) {")
     lines.append("#pragma unroll 1")
     lines.append("    for (int ib = b0; ib < b1; ++ib) {")
     lines.append("        const PrimPair<R> pb = P.load(ib);")
     lines.append("#pragma unroll 1")
     lines.append("        for (int ik = k0; ik < k1; ++ik) {")
     lines.append("            const PrimPair<R> pk = P.load(ik);")
-    lines.append("            const R rz = R(1) / (pb.zeta + pk.zeta);")
-    lines.append("            const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;")
-    lines.append("            const R oo2z = pb.oo2z, oo2e = pk.oo2z;")
-    lines.append("            (void)roe; (void)roz; (void)oo2ze; (void)oo2z; (void)oo2e;")
-    lines.append("            const R PQx = pb.PAx - pk.PAx + ACx, PQy = pb.PAy - pk.PAy + ACy, PQz = pb.PAz - pk.PAz + ACz;")
-    lines.append("            const R PAx = pb.PAx, PAy = pb.PAy, PAz = pb.PAz;")
-    lines.append("            const R QCx = pk.PAx, QCy = pk.PAy, QCz = pk.PAz;")
-    lines.append("            const R WPx = -roz * PQx, WPy = -roz * PQy, WPz = -roz * PQz;")
-    lines.append("            const R WQx = roe * PQx, WQy = roe * PQy, WQz = roe * PQz;")
-    lines.append("            (void)PAx; (void)PAy; (void)PAz; (void)QCx; (void)QCy; (void)QCz;")
-    lines.append("            (void)WPx; (void)WPy; (void)WPz; (void)WQx; (void)WQy; (void)WQz;")
-    lines.append("            const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);")
-    lines.append("            const R pref = pb.K * pk.K * prefactor_sqrt(rz);")
-    lines.append(f"            R F[{L + 1}];")
-    lines.append(f"            boys_eval<R, {L}, BMODE>(T, F, P.boys64, P.boys32);")
-    lines.append("#pragma unroll")
-    lines.append(f"            for (int m = 0; m <= {L}; ++m) F[m] *= pref;")
-    body = []
-    vflops = v.emit(body, "            ")
     lines += body
-    for ei, e in enumerate(v.es):
-        for fi, f in enumerate(v.fs):
-            lines.append(f"            acc[{ei * len(v.fs) + fi}] += {v.names[(e, f, 0)]};")
     lines.append("        }")
+    lines.append("    }")
+    lines.append("    } else {")
+    lines.append("    // the G lanes of a group split the primitive quartets (flattened index g, g + G, ...)")
+    lines.append("    int ib = b0, ik = k0 + g;")
+    lines.append("    while (ik >= k1) { ik -= nk; ++ib; }")
+    lines.append("#pragma unroll 1")
+    lines.append("    while (ib < b1) {")
+    lines.append("        {")
+    lines.append("            const PrimPair<R> pb = P.load(ib);")
+    lines.append("            const PrimPair<R> pk = P.load(ik);")
+    lines += body
+    lines.append("        }")
+    lines.append("        ik += G;")
+    lines.append("        while (ik >= k1) { ik -= nk; ++ib; }")
+    lines.append("    }")
+    lines.append("#pragma unroll")
+    lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = group_sum<G>(acc[k]);")
     lines.append("    }")
     lines.append("    const R ABx = R(P.AB[3 * bp]), ABy = R(P.AB[3 * bp + 1]), ABz = R(P.AB[3 * bp + 2]);")
     lines.append("    const R CDx = R(P.AB[3 * kp]), CDy = R(P.AB[3 * kp + 1]), CDz = R(P.AB[3 * kp + 2]);")
@@ -489,9 +664,31 @@ def emit_class(cls):
     L.append("};")
     L.append(f"__device__ const int fslot_{t}[{len(pr['fin'])}] = {{" + ", ".join(str(a) for a, _ in pr["fin"]) + "};")
     L.append(f"__device__ const double fscale_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(b) for _, b in pr["fin"]) + "};")
-    L.append("template <typename R, int BMODE>")
-    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, R* I)")
+    tp = build_team_program(cls)
+    info["team_nvi"], info["team_nh"] = max(tp["nv"], tp["nint"]), tp["nh"]
+    L.append(f"// level-scheduled program for the warp-per-quartet J/K kernel: {len(tp['vlev']) - 1} VRR levels, "
+             f"{len(tp['hlev']) - 1} HRR levels, {tp['nv']} + {tp['nh']} shared-memory slots")
+    L.append(f"__device__ const uint4 tvprog_{t}[{len(tp['vrr'])}] = {{")
+    for (kind, tg, s1, s2, s3, s4, s5, d, m1, m2) in tp["vrr"]:
+        w0 = kind | (d << 2) | (m1 << 4) | (m2 << 8) | (tg << 16)
+        L.append(f"    {{{w0}u, {s1 | (s2 << 16)}u, {s3 | (s4 << 16)}u, {s5}u}},")
+    L.append("};")
+    L.append(f"__device__ const int tvlev_{t}[{len(tp['vlev'])}] = {{" + ", ".join(map(str, tp["vlev"])) + "};")
+    L.append(f"__device__ const uint2 thprog_{t}[{len(tp['hrr'])}] = {{")
+    for (tg, s1, s2, d, side) in tp["hrr"]:
+        L.append(f"    {{{tg | (d << 16) | (side << 18)}u, {s1 | (s2 << 16)}u}},")
+    L.append("};")
+    L.append(f"__device__ const int thlev_{t}[{len(tp['hlev'])}] = {{" + ", ".join(map(str, tp["hlev"])) + "};")
+    L.append(f"__device__ const int tfslot_{t}[{len(tp['fin'])}] = {{" + ", ".join(str(a) for a, _ in tp["fin"]) + "};")
+    L.append(f"__device__ const double tfscale_{t}[{len(tp['fin'])}] = {{" + ", ".join(repr(b) for _, b in tp["fin"]) + "};")
+    L.append(f"#define MESS_TEAM_ARGS_{t} {tp['L']}, {max(tp['nv'], tp['nint'])}, {tp['nh']}, {tp['nacc']}, "
+             f"{len(tp['vlev']) - 1}, {len(tp['hlev']) - 1}, {tp['nint']}, {tp['na']}, {tp['nb']}, {tp['nc']}, {tp['nd']}")
+    L.append(f"#define MESS_TEAM_PROG_{t} tvprog_{t}, tvlev_{t}, thprog_{t}, thlev_{t}, tfslot_{t}, tfscale_{t}")
+    L.append("template <typename R, int BMODE, int G>")
+    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I)")
     L.append("{")
+    L.append("    static_assert(G == 1, \"op-program classes run one thread per quartet\");")
+    L.append("    (void)g;")
     L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
              f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kp, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, I);")
     L.append("}")
@@ -572,6 +769,9 @@ def main(outdir):
         diag = (la, lb) == (lc, ld)
         u = ["// Generated by gen_eri.py: do not edit.", f'#include "eri_class_{t}.cuh"', '#include "eri_launch.h"', "",
              f"MESS_DEFINE_CLASS_KERNELS({t}, {na}, {nb}, {nc}, {nd})"]
+        team = info["mode"] == "program"
+        if team:
+            u.append(f"MESS_DEFINE_TEAM_KERNEL({t})")
         if diag:
             u.append(f"MESS_DEFINE_SCHWARZ_KERNEL({t}, {na}, {nb})")
         u += ["", f"cudaError_t mess_launch_{t}(const ClassLaunchArgs& a)", "{",
@@ -591,12 +791,37 @@ def main(outdir):
               "    const dim3 g((unsigned)nblk);",
               "    if (a.kind == MESS_KIND_STORE) {",
               f"        k_store_{t}<<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.out, a.n);",
-              "    } else if (a.mode == MESS_MODE_FP64) {",
-              f"        k_jk_{t}<double, 0><<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
-              "    } else if (a.mode == MESS_MODE_MIXED) {",
-              f"        k_jk_{t}<float, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
               "    } else {",
-              f"        k_jk_{t}<float, 2><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              ] + ([
+              "        static int cfg[3][64];   // dynamic shared memory opt-in done, per kernel mode and device",
+              "        const long long nbt = (a.bin.total + MESS_TEAM_WARPS - 1) / MESS_TEAM_WARPS;",
+              "        if (nbt > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
+              "        const dim3 gt((unsigned)nbt);",
+              "        if (a.mode == MESS_MODE_FP64)",
+              f"            return mess_team_launch<double, 0>(k_jk_team_{t}<double, 0>, gt, team_smem_{t}<double>(), a, *a.P64_ptr, cfg[0]);",
+              "        else if (a.mode == MESS_MODE_MIXED)",
+              f"            return mess_team_launch<float, 1>(k_jk_team_{t}<float, 1>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[1]);",
+              "        else",
+              f"            return mess_team_launch<float, 2>(k_jk_team_{t}<float, 2>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[2]);",
+              ] if info["mode"] == "program" else []) + ([
+              "        if (a.G == 8) {",
+              "            const long long nb8 = (a.bin.total * 8 + T - 1) / T;",
+              "            if (nb8 > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
+              "            const dim3 g8((unsigned)nb8);",
+              "            if (a.mode == MESS_MODE_FP64)",
+              f"                k_jk_{t}<double, 0, 8><<<g8, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
+              "            else if (a.mode == MESS_MODE_MIXED)",
+              f"                k_jk_{t}<float, 1, 8><<<g8, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              "            else",
+              f"                k_jk_{t}<float, 2, 8><<<g8, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              "            return cudaGetLastError();",
+              "        }"] if info["mode"] == "straight" else []) + [
+              "        if (a.mode == MESS_MODE_FP64)",
+              f"            k_jk_{t}<double, 0, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
+              "        else if (a.mode == MESS_MODE_MIXED)",
+              f"            k_jk_{t}<float, 1, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              "        else",
+              f"            k_jk_{t}<float, 2, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
               "    }",
               "    return cudaGetLastError();",
               "}"]

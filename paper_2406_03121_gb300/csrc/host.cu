@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <fstream>
 #include <map>
+#include <mutex>
+#include <numeric>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -207,6 +209,10 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
                 }
                 bp.nbra = (int)bra.size() - bp.bra_off;
                 offs.push_back(bp.total);
+                // heavily contracted quartets: split the primitive loop over 8 lanes
+                const bool straight = MESS_QCLASS[bp.qclass].nacc <= 96 && MESS_QCLASS[bp.qclass].nvrr <= 280;
+                const double avg = bp.total > 0 ? (double)bp.prim_quartets / (double)bp.total : 0.0;
+                bp.G = (straight && avg >= 24.0) ? 8 : 1;
                 if (bp.nbra > 0) B.parts.push_back(bp);
                 else offs.resize(bp.offs_off);
             }
@@ -221,6 +227,39 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
     B.tau64 = tau64;
     B.split = split;
     return MESS_OK;
+}
+
+// ------------------------------------------------------------------------------------------ streams
+// Per-device pool of non-blocking streams: the class launches of one J/K build fork from the
+// caller's stream, run concurrently (most of them are small), and join back before the
+// symmetrisation.  Fork/join is by events, so a captured caller stream captures the whole build.
+#define MESS_NSTREAMS 8
+struct StreamPool {
+    bool init = false;
+    cudaStream_t s[MESS_NSTREAMS];
+    cudaEvent_t fork, join[MESS_NSTREAMS];
+    std::mutex mu;
+};
+static StreamPool g_pools[64];
+
+static cudaError_t get_pool(StreamPool** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    StreamPool& P = g_pools[dev];
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (!P.init) {
+        for (int i = 0; i < MESS_NSTREAMS; ++i) {
+            if ((e = cudaStreamCreateWithFlags(&P.s[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&P.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        P.init = true;
+    }
+    *out = &P;
+    return cudaSuccess;
 }
 
 static BinLaunch bin_launch(const mess_basis* b, const BinPart& p)
@@ -555,13 +594,34 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
         ev.resize(2 * b->bins.parts.size());
         for (auto& e : ev) MESS_CUDA_TRY(cudaEventCreate(&e));
     }
+    // launch order: most expensive parts first (FP64, then by algorithmic work)
+    std::vector<size_t> order(b->bins.parts.size());
+    std::iota(order.begin(), order.end(), (size_t)0);
+    auto cost = [&](const BinPart& p) {
+        double fp, fs;
+        class_flops(p.qclass, &fp, &fs);
+        return (fp * (double)p.prim_quartets + fs * (double)p.total) * (p.fp64 ? 62.0 : 1.0);
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return cost(b->bins.parts[x]) > cost(b->bins.parts[y]); });
+    StreamPool* pool = nullptr;
+    std::unique_lock<std::mutex> lk;
+    const bool concurrent = !parts && b->bins.parts.size() > 1;
+    if (concurrent) {
+        MESS_CUDA_TRY(get_pool(&pool));
+        lk = std::unique_lock<std::mutex>(pool->mu);
+        MESS_CUDA_TRY(cudaEventRecord(pool->fork, s));
+        for (int i = 0; i < MESS_NSTREAMS; ++i) MESS_CUDA_TRY(cudaStreamWaitEvent(pool->s[i], pool->fork, 0));
+    }
     mess_jk_info inf{};
     mess_status out = MESS_OK;
-    for (size_t k = 0; k < b->bins.parts.size(); ++k) {
+    for (size_t r = 0; r < order.size(); ++r) {
+        const size_t k = order[r];
         const BinPart& p = b->bins.parts[k];
         ClassLaunchArgs a{};
         a.kind = MESS_KIND_JK;
         a.mode = p.fp64 ? MESS_MODE_FP64 : (o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);
+        a.G = p.G;
         a.bin = bin_launch(b, p);
         a.P64_ptr = &b->P64;
         a.P32_ptr = &b->P32;
@@ -569,7 +629,7 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
         a.J = dJ;
         a.K = dK;
         a.n = n;
-        a.stream = s;
+        a.stream = concurrent ? pool->s[r % MESS_NSTREAMS] : s;
         if (parts) cudaEventRecord(ev[2 * k], s);
         cudaError_t e = MESS_CLASS_LAUNCHERS[p.qclass](a);
         if (parts) cudaEventRecord(ev[2 * k + 1], s);
@@ -583,6 +643,13 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
         inf.primitive_quartets += p.prim_quartets;
         if (p.fp64) inf.shell_quartets_fp64 += p.total;
         inf.kernel_launches += 1;
+    }
+    if (concurrent) {
+        // join: the caller's stream waits for every pool stream (also after a failed launch)
+        for (int i = 0; i < MESS_NSTREAMS; ++i) {
+            cudaEventRecord(pool->join[i], pool->s[i]);
+            cudaStreamWaitEvent(s, pool->join[i], 0);
+        }
     }
     if (out == MESS_OK) {
         cudaError_t e = mess_launch_symmetrise_jk(dJ, dK, n, s);

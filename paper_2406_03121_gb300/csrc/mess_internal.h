@@ -56,6 +56,7 @@ struct HostShell {
 struct BinPart {
     int qclass;
     int fp64;              // 1: evaluated in FP64
+    int G;                 // lanes per shell quartet (primitive loop split across G lanes)
     int bra_off, nbra;     // into the concatenated bra / kbeg / offs arrays
     int ket_list;          // pair class of the ket list
     long long total;       // shell quartets
