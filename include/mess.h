@@ -142,11 +142,19 @@ mess_status mess_schwarz(const mess_basis* b, double* Q);
 
 /* Closed-shell Roothaan SCF (paper Eq. 2, Sec. 3): Loewdin orthogonalisation, core-Hamiltonian
  * guess, Pulay DIIS on FDS - SDF, converged when |dE| < conv_E and max|FDS - SDF| < conv_comm.
+ * Runs entirely on the GPU: one-electron integrals, Loewdin X (Jacobi eigensolver), the J/K builds of
+ * mess_jk_build_device with opts->prec / schwarz_tau / fp64_tau, F = H + J - K/2, DIIS, the
+ * diagonalisation of X^T F X (one thread block per molecule, cyclic Jacobi, FP64) and D = 2 C_occ C_occ^T.
  * D_out (nullable): host n*n final density.  Errors: MESS_ENOCONV (res holds the last iterate),
- * MESS_EINVAL (odd electron count), MESS_ENOMEM, MESS_ECUDA, MESS_ENUMERIC. */
+ * MESS_EINVAL (odd electron count), MESS_ENOTIMPL (n > 256 or a guess other than MESS_GUESS_CORE),
+ * MESS_ENOMEM, MESS_ECUDA, MESS_ENUMERIC (singular overlap, non-finite energy). */
 mess_status mess_scf(const mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* D_out);
 
-/* Batched SCF over many molecules (the paper's vmap over conformers, Sec. 5.2).  res: nmol entries. */
+/* Batched SCF over many molecules (the paper's vmap over conformers, Sec. 5.2): every molecule of
+ * bases[0..nmol) (single-molecule bases, any sizes) in the same kernel launches - the J/K kernels
+ * take quartets of all molecules from one set of bins; Fock, DIIS, Jacobi and the density run one
+ * block per molecule; converged molecules drop out.  res: nmol entries (caller-owned).
+ * Errors: as mess_scf; MESS_ENOCONV if any molecule did not converge. */
 mess_status mess_scf_batch(int nmol, mess_basis* const* bases, const mess_scf_opts* opts, mess_scf_result* res);
 
 /* One kernel launch of a profiled J/K build. */

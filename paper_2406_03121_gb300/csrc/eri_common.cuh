@@ -24,6 +24,9 @@ template <typename R> struct PairTable {
     const int* __restrict__ fb;              // [npair] first function of B
     const int* __restrict__ same;            // [npair] 1 if A == B (same shell)
     const double* __restrict__ C;            // [npair][3] centre of the pair's first shell A
+    const int* __restrict__ mol;             // [npair] molecule of the pair (batched bases)
+    const long long* __restrict__ mbase;     // [nmol] offset of the molecule's n x n block (packed matrices)
+    const int* __restrict__ mn;              // [nmol] basis functions of the molecule (row stride)
     const double* __restrict__ boys64;       // Boys grid, FP64
     const float* __restrict__ boys32;        // Boys grid, FP32
 
@@ -251,7 +254,12 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         R I[(NA) * (NB) * (NC) * (ND)];                                                             \
         eri_##TAG<R, BMODE, G>(P, bp, kp, g, I);                                                    \
         DigestCtx c;                                                                                \
-        c.D = D; c.J = J; c.K = K; c.n = n;                                                         \
+        {                                                                                           \
+            const int m_ = __ldg(P.mol + bp);                                                       \
+            const long long o_ = __ldg(P.mbase + m_);                                               \
+            c.D = D + o_; c.J = J + o_; c.K = K + o_; c.n = __ldg(P.mn + m_);                       \
+        }                                                                                           \
+        (void)n;                                                                                    \
         c.fa = __ldg(P.fa + bp); c.fb = __ldg(P.fb + bp);                                           \
         c.fc = __ldg(P.fa + kp); c.fd = __ldg(P.fb + kp);                                           \
         R s = valid ? R(1) : R(0);                                                                  \
@@ -506,7 +514,13 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     if (__ldg(P.same + kp)) s *= R(0.5);
     if (bp == kp) s *= R(0.5);
     const int fa = __ldg(P.fa + bp), fb = __ldg(P.fb + bp), fc = __ldg(P.fa + kp), fd = __ldg(P.fb + kp);
-    const size_t nn = (size_t)n;
+    const int mol_ = __ldg(P.mol + bp);
+    const long long off_ = __ldg(P.mbase + mol_);
+    D += off_;
+    J += off_;
+    K += off_;
+    const size_t nn = (size_t)__ldg(P.mn + mol_);
+    (void)n;
 #define MESS_I(a_, b_, c_, d_) I[(((a_) * NB + (b_)) * NC + (c_)) * ND + (d_)]
     for (int o = lane; o < NA * NB; o += 32) {          // J_ab = sum_cd I D_cd
         const int a = o / NB, bb = o % NB;

@@ -143,7 +143,7 @@ void normalise_shell(HostShell& s, const std::vector<double>& d)
 mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
 {
     BinSet& B = b->bins;
-    if (B.tau == tau && B.tau64 == tau64 && B.split == split) return MESS_OK;
+    if (B.tau == tau && B.tau64 == tau64 && B.split == split && B.active_version == b->active_version) return MESS_OK;
     B.parts.clear();
     std::vector<int> bra, kbeg;
     std::vector<long long> offs;
@@ -164,16 +164,6 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
                 fpre[j + 1] = fpre[j] + nfp;
                 ppre[j + 1] = ppre[j] + b->pp_n[pk];
             }
-            // number of kets j (Q descending) with qi * qk[j] >= t
-            auto count_ge = [&](double qi, double t) -> int {
-                if (t <= 0.0) return nk;
-                int lo = 0, hi = nk;   // first j with qi*qk[j] < t
-                while (lo < hi) {
-                    int mid = (lo + hi) / 2;
-                    if (qi * qk[mid] >= t) lo = mid + 1; else hi = mid;
-                }
-                return lo;
-            };
             const int nparts = split == 2 ? 2 : 1;
             for (int part = 0; part < nparts; ++part) {
                 const int fp64 = split == 0 ? 1 : (split == 1 ? 0 : (part == 0 ? 1 : 0));
@@ -186,26 +176,43 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
                 bp.total = 0;
                 bp.fn_quartets = 0;
                 bp.prim_quartets = 0;
-                for (int i = 0; i < (int)bl.size(); ++i) {
-                    const int pb = bl[i];
-                    const double qi = b->Q[pb];
-                    int cnt = count_ge(qi, tau);
-                    if (same) cnt = std::min(cnt, i + 1);
-                    int beg = 0, end = cnt;
-                    if (split == 2) {
-                        const int c64 = tau64 > 0.0 ? std::min(count_ge(qi, tau64), cnt) : 0;
-                        if (part == 0) end = c64; else beg = c64;
+                for (int m = 0; m < b->nmol; ++m) {
+                    if (!b->active[m]) continue;
+                    const int bs0 = b->class_seg[p1][m], bs1 = b->class_seg[p1][m + 1];
+                    const int ks0 = b->class_seg[p2][m], ks1 = b->class_seg[p2][m + 1];
+                    if (bs1 == bs0 || ks1 == ks0) continue;
+                    // kets j in [ks0, ks1) (Q descending) with qi * qk[j] >= t: a prefix of the segment
+                    auto count_ge = [&](double qi, double t) -> int {
+                        if (t <= 0.0) return ks1 - ks0;
+                        int lo = ks0, hi = ks1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) / 2;
+                            if (qi * qk[mid] >= t) lo = mid + 1; else hi = mid;
+                        }
+                        return lo - ks0;
+                    };
+                    for (int i = bs0; i < bs1; ++i) {
+                        const int il = i - bs0;
+                        const int pb = bl[i];
+                        const double qi = b->Q[pb];
+                        int cnt = count_ge(qi, tau);
+                        if (same) cnt = std::min(cnt, il + 1);
+                        int beg = 0, end = cnt;
+                        if (split == 2) {
+                            const int c64 = tau64 > 0.0 ? std::min(count_ge(qi, tau64), cnt) : 0;
+                            if (part == 0) end = c64; else beg = c64;
+                        }
+                        if (end <= beg) continue;
+                        bra.push_back(pb);
+                        kbeg.push_back(ks0 + beg);
+                        offs.push_back(bp.total);
+                        bp.total += end - beg;
+                        const int na = ncart(b->shells[b->pair_a[pb]].l), nb = ncart(b->shells[b->pair_b[pb]].l);
+                        const long long nfb = b->pair_a[pb] == b->pair_b[pb] ? (long long)na * (na + 1) / 2 : (long long)na * nb;
+                        bp.fn_quartets += nfb * (fpre[ks0 + end] - fpre[ks0 + beg]);
+                        if (same && beg <= il && il < end) bp.fn_quartets += nfb * (nfb + 1) / 2 - nfb * nfb;
+                        bp.prim_quartets += (long long)b->pp_n[pb] * (ppre[ks0 + end] - ppre[ks0 + beg]);
                     }
-                    if (end <= beg) continue;
-                    bra.push_back(pb);
-                    kbeg.push_back(beg);
-                    offs.push_back(bp.total);
-                    bp.total += end - beg;
-                    const int na = ncart(b->shells[b->pair_a[pb]].l), nb = ncart(b->shells[b->pair_b[pb]].l);
-                    const long long nfb = b->pair_a[pb] == b->pair_b[pb] ? (long long)na * (na + 1) / 2 : (long long)na * nb;
-                    bp.fn_quartets += nfb * (fpre[end] - fpre[beg]);
-                    if (same && beg <= i && i < end) bp.fn_quartets += nfb * (nfb + 1) / 2 - nfb * nfb;
-                    bp.prim_quartets += (long long)b->pp_n[pb] * (ppre[end] - ppre[beg]);
                 }
                 bp.nbra = (int)bra.size() - bp.bra_off;
                 offs.push_back(bp.total);
@@ -226,6 +233,7 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
     B.tau = tau;
     B.tau64 = tau64;
     B.split = split;
+    B.active_version = b->active_version;
     return MESS_OK;
 }
 
@@ -275,13 +283,47 @@ static BinLaunch bin_launch(const mess_basis* b, const BinPart& p)
 }
 
 // ------------------------------------------------------------------------------------------ create
-static mess_status build_basis(mess_basis* b, const char* basis_file)
+// Append one molecule (atoms and already normalised shells) to a basis under construction.
+static void add_molecule(mess_basis* b, const std::vector<int>& Z, const std::vector<double>& xyz,
+                         const std::vector<HostShell>& shells)
 {
-    std::map<std::string, std::vector<FileShell>> data;
-    if (!parse_basis_file(basis_file, data)) return MESS_EINVAL;
-    int f0 = 0;
-    for (int a = 0; a < b->natom; ++a) {
-        const int z = b->Z[a];
+    const int m = (int)b->mol_nbf.size();
+    const int atom0 = b->natom;
+    b->mol_atom_off.push_back(atom0);
+    b->mol_atom_n.push_back((int)Z.size());
+    b->mol_shell_off.push_back((int)b->shells.size());
+    b->mol_shell_n.push_back((int)shells.size());
+    int fl = 0, nel = 0;
+    for (HostShell s : shells) {
+        s.atom = s.atom + atom0;
+        s.mol = m;
+        s.fl = fl;
+        s.f0 = b->nbf + fl;
+        fl += ncart(s.l);
+        b->shells.push_back(s);
+    }
+    for (int z : Z) nel += z;
+    b->Z.insert(b->Z.end(), Z.begin(), Z.end());
+    b->xyz.insert(b->xyz.end(), xyz.begin(), xyz.end());
+    b->natom += (int)Z.size();
+    b->mol_base.push_back(b->packed);
+    b->packed += (long long)fl * fl;
+    b->mol_nbf.push_back(fl);
+    b->mol_nelec.push_back(nel);
+    b->nbf += fl;
+    b->nelec += nel;
+    b->max_nbf = std::max(b->max_nbf, fl);
+    b->nmol = m + 1;
+    b->active.push_back(1);
+}
+
+// Shells of one structure from a parsed basis file, normalised (molecule-local atom indices).
+static mess_status shells_from_file(int natom, const int* Z, const double* xyz,
+                                    const std::map<std::string, std::vector<FileShell>>& data,
+                                    const char* basis_file, std::vector<HostShell>& out)
+{
+    for (int a = 0; a < natom; ++a) {
+        const int z = Z[a];
         if (z <= 0 || z > 10) { mess_set_error("unsupported atomic number %d", z); return MESS_EINVAL; }
         auto it = data.find(kSymbols[z]);
         if (it == data.end()) { mess_set_error("element %s not in basis file %s", kSymbols[z], basis_file); return MESS_EINVAL; }
@@ -291,74 +333,79 @@ static mess_status build_basis(mess_basis* b, const char* basis_file)
             s.l = fs.l;
             s.K = (int)fs.a.size();
             s.atom = a;
-            s.f0 = f0;
-            for (int x = 0; x < 3; ++x) s.R[x] = b->xyz[3 * a + x];
+            s.f0 = s.fl = 0;
+            s.mol = 0;
+            for (int x = 0; x < 3; ++x) s.R[x] = xyz[3 * a + x];
             s.alpha = fs.a;
             normalise_shell(s, fs.d);
-            f0 += ncart(s.l);
-            b->shells.push_back(s);
+            out.push_back(s);
         }
-        b->nelec += z;
     }
-    b->nbf = f0;
-    // per-function component scale sqrt((2L-1)!! / ((2l-1)!!(2m-1)!!(2n-1)!!))
-    for (const HostShell& s : b->shells)
-        for (int lx = s.l; lx >= 0; --lx)
-            for (int ly = s.l - lx; ly >= 0; --ly) {
-                const int lz = s.l - lx - ly;
-                b->fscale.push_back(sqrt(dfact(2 * s.l - 1) / (dfact(2 * lx - 1) * dfact(2 * ly - 1) * dfact(2 * lz - 1))));
-            }
     return MESS_OK;
 }
 
 static mess_status build_pairs(mess_basis* b)
 {
-    const int ns = (int)b->shells.size();
+    // per-function component scale sqrt((2L-1)!! / ((2l-1)!!(2m-1)!!(2n-1)!!)) and local index
+    b->fscale.clear();
+    b->f_local.clear();
+    for (const HostShell& s : b->shells) {
+        int k = 0;
+        for (int lx = s.l; lx >= 0; --lx)
+            for (int ly = s.l - lx; ly >= 0; --ly, ++k) {
+                const int lz = s.l - lx - ly;
+                b->fscale.push_back(sqrt(dfact(2 * s.l - 1) / (dfact(2 * lx - 1) * dfact(2 * ly - 1) * dfact(2 * lz - 1))));
+                b->f_local.push_back(s.fl + k);
+            }
+    }
     std::vector<PrimPairRec<double>> pp64;
     std::vector<PrimPairRec<float>> pp32;
     std::vector<double> AB, Ccen;
     std::vector<int> fa, fb, same;
     const double kpref = sqrt(2.0) * pow(M_PI, 1.25);
-    for (int A = 0; A < ns; ++A) {
-        for (int B = 0; B < ns; ++B) {
-            const HostShell& sa = b->shells[A];
-            const HostShell& sb = b->shells[B];
-            const bool canonical = sa.l > sb.l || (sa.l == sb.l && A >= B);
-            if (!canonical) continue;
-            const int p = b->npair++;
-            b->pair_a.push_back(A);
-            b->pair_b.push_back(B);
-            b->pair_class.push_back(pclass_of(sa.l, sb.l));
-            b->pp_off.push_back((int)pp64.size());
-            double ab[3], ab2 = 0.0;
-            for (int x = 0; x < 3; ++x) {
-                ab[x] = sa.R[x] - sb.R[x];
-                ab2 += ab[x] * ab[x];
-                AB.push_back(ab[x]);
-                Ccen.push_back(sa.R[x]);
-            }
-            for (int i = 0; i < sa.K; ++i)
-                for (int j = 0; j < sb.K; ++j) {
-                    const double al = sa.alpha[i], be = sb.alpha[j], z = al + be;
-                    PrimPairRec<double> r{};
-                    r.v[0] = z;
-                    for (int x = 0; x < 3; ++x) {
-                        const double P = (al * sa.R[x] + be * sb.R[x]) / z;
-                        r.v[1 + x] = P;
-                        r.v[4 + x] = P - sa.R[x];
-                    }
-                    r.v[7] = kpref * sa.coef[i] * sb.coef[j] * exp(-al * be / z * ab2) / z;
-                    r.v[8] = 0.5 / z;
-                    pp64.push_back(r);
-                    PrimPairRec<float> f{};
-                    for (int k = 0; k < 12; ++k) f.v[k] = (float)r.v[k];
-                    pp32.push_back(f);
+    for (int m = 0; m < b->nmol; ++m) {
+        const int s0 = b->mol_shell_off[m], s1 = s0 + b->mol_shell_n[m];
+        for (int A = s0; A < s1; ++A) {
+            for (int B = s0; B < s1; ++B) {
+                const HostShell& sa = b->shells[A];
+                const HostShell& sb = b->shells[B];
+                const bool canonical = sa.l > sb.l || (sa.l == sb.l && A >= B);
+                if (!canonical) continue;
+                b->npair++;
+                b->pair_a.push_back(A);
+                b->pair_b.push_back(B);
+                b->pair_class.push_back(pclass_of(sa.l, sb.l));
+                b->pair_mol.push_back(m);
+                b->pp_off.push_back((int)pp64.size());
+                double ab[3], ab2 = 0.0;
+                for (int x = 0; x < 3; ++x) {
+                    ab[x] = sa.R[x] - sb.R[x];
+                    ab2 += ab[x] * ab[x];
+                    AB.push_back(ab[x]);
+                    Ccen.push_back(sa.R[x]);
                 }
-            b->pp_n.push_back(sa.K * sb.K);
-            fa.push_back(sa.f0);
-            fb.push_back(sb.f0);
-            same.push_back(A == B ? 1 : 0);
-            (void)p;
+                for (int i = 0; i < sa.K; ++i)
+                    for (int j = 0; j < sb.K; ++j) {
+                        const double al = sa.alpha[i], be = sb.alpha[j], z = al + be;
+                        PrimPairRec<double> r{};
+                        r.v[0] = z;
+                        for (int x = 0; x < 3; ++x) {
+                            const double P = (al * sa.R[x] + be * sb.R[x]) / z;
+                            r.v[1 + x] = P;
+                            r.v[4 + x] = P - sa.R[x];
+                        }
+                        r.v[7] = kpref * sa.coef[i] * sb.coef[j] * exp(-al * be / z * ab2) / z;
+                        r.v[8] = 0.5 / z;
+                        pp64.push_back(r);
+                        PrimPairRec<float> f{};
+                        for (int k = 0; k < 12; ++k) f.v[k] = (float)r.v[k];
+                        pp32.push_back(f);
+                    }
+                b->pp_n.push_back(sa.K * sb.K);
+                fa.push_back(sa.fl);
+                fb.push_back(sb.fl);
+                same.push_back(A == B ? 1 : 0);
+            }
         }
     }
     MESS_CUDA_TRY(b->d_pp64.upload(pp64));
@@ -375,6 +422,12 @@ static mess_status build_pairs(mess_basis* b)
     MESS_CUDA_TRY(b->d_boys64.upload(tab));
     std::vector<float> tab32(tab.begin(), tab.end());
     MESS_CUDA_TRY(b->d_boys32.upload(tab32));
+    MESS_CUDA_TRY(b->d_pair_mol.upload(b->pair_mol));
+    MESS_CUDA_TRY(b->d_mol_base.upload(b->mol_base));
+    MESS_CUDA_TRY(b->d_mol_n.upload(b->mol_nbf));
+    MESS_CUDA_TRY(b->d_mol_atom_off.upload(b->mol_atom_off));
+    MESS_CUDA_TRY(b->d_mol_atom_n.upload(b->mol_atom_n));
+    MESS_CUDA_TRY(b->d_f_local.upload(b->f_local));
     b->P64.pp = b->d_pp64.p;
     b->P32.pp = b->d_pp32.p;
     b->P64.pp_off = b->P32.pp_off = b->d_pp_off.p;
@@ -384,6 +437,9 @@ static mess_status build_pairs(mess_basis* b)
     b->P64.fb = b->P32.fb = b->d_fb.p;
     b->P64.same = b->P32.same = b->d_same.p;
     b->P64.C = b->P32.C = b->d_Ccen.p;
+    b->P64.mol = b->P32.mol = b->d_pair_mol.p;
+    b->P64.mbase = b->P32.mbase = b->d_mol_base.p;
+    b->P64.mn = b->P32.mn = b->d_mol_n.p;
     b->P64.boys64 = b->P32.boys64 = b->d_boys64.p;
     b->P64.boys32 = b->P32.boys32 = b->d_boys32.p;
     // shells for the one-electron kernels
@@ -434,22 +490,33 @@ static mess_status build_schwarz(mess_basis* b)
     MESS_CUDA_TRY(cudaMemcpy(b->Q.data(), b->d_Q.p, sizeof(double) * b->npair, cudaMemcpyDeviceToHost));
     for (int p = 0; p < b->npair; ++p)
         if (!std::isfinite(b->Q[p])) { mess_set_error("non-finite Schwarz factor for pair %d", p); return MESS_ENUMERIC; }
+    // class lists: per molecule, pairs sorted by Q descending
     for (int c = 0; c < MESS_NUM_PCLASS; ++c) {
-        std::vector<int> l = lists[c];
-        std::stable_sort(l.begin(), l.end(), [&](int x, int y) { return b->Q[x] > b->Q[y]; });
+        std::vector<std::vector<int>> per(b->nmol);
+        for (int p : lists[c]) per[b->pair_mol[p]].push_back(p);
+        std::vector<int> l;
+        std::vector<int> seg(1, 0);
+        for (int m = 0; m < b->nmol; ++m) {
+            std::stable_sort(per[m].begin(), per[m].end(), [&](int x, int y) { return b->Q[x] > b->Q[y]; });
+            l.insert(l.end(), per[m].begin(), per[m].end());
+            seg.push_back((int)l.size());
+        }
         b->class_list[c] = l;
+        b->class_seg[c] = seg;
         MESS_CUDA_TRY(b->d_class_list[c].upload(l));
     }
     return MESS_OK;
 }
 
-static void free_basis(mess_basis* b)
+void mess_free_basis(mess_basis* b)
 {
     b->d_pp64.free(); b->d_pp32.free(); b->d_pp_off.free(); b->d_pp_n.free(); b->d_fa.free();
     b->d_fb.free(); b->d_same.free(); b->d_AB.free(); b->d_Ccen.free(); b->d_Q.free(); b->d_boys64.free();
     b->d_boys32.free(); b->d_Z.free(); b->d_xyz.free(); b->d_shell_l.free(); b->d_shell_K.free();
     b->d_shell_f0.free(); b->d_shell_poff.free(); b->d_shell_R.free(); b->d_shell_alpha.free();
     b->d_shell_coef.free(); b->d_fscale.free(); b->d_pair_a.free(); b->d_pair_b.free();
+    b->d_pair_mol.free(); b->d_mol_n.free(); b->d_mol_atom_off.free(); b->d_mol_atom_n.free();
+    b->d_f_local.free(); b->d_mol_base.free();
     for (auto& d : b->d_class_list) d.free();
     b->bins.bra.free(); b->bins.kbeg.free(); b->bins.offs.free();
 }
@@ -462,15 +529,34 @@ extern "C" mess_status mess_basis_create(int natom, const int* Z, const double* 
     if (natom <= 0 || !Z || !xyz_bohr || !basis_file) { mess_set_error("bad structure arguments"); return MESS_EINVAL; }
     for (int i = 0; i < 3 * natom; ++i)
         if (!std::isfinite(xyz_bohr[i])) { mess_set_error("non-finite coordinate"); return MESS_EINVAL; }
+    std::map<std::string, std::vector<FileShell>> data;
+    if (!parse_basis_file(basis_file, data)) return MESS_EINVAL;
+    std::vector<HostShell> shells;
+    mess_status st = shells_from_file(natom, Z, xyz_bohr, data, basis_file, shells);
+    if (st != MESS_OK) return st;
     mess_basis* b = new (std::nothrow) mess_basis();
     if (!b) { mess_set_error("host allocation failed"); return MESS_ENOMEM; }
-    b->natom = natom;
-    b->Z.assign(Z, Z + natom);
-    b->xyz.assign(xyz_bohr, xyz_bohr + 3 * natom);
-    mess_status st = build_basis(b, basis_file);
-    if (st == MESS_OK) st = build_pairs(b);
+    add_molecule(b, std::vector<int>(Z, Z + natom), std::vector<double>(xyz_bohr, xyz_bohr + 3 * natom), shells);
+    st = build_pairs(b);
     if (st == MESS_OK) st = build_schwarz(b);
-    if (st != MESS_OK) { free_basis(b); delete b; return st; }
+    if (st != MESS_OK) { mess_free_basis(b); delete b; return st; }
+    *out = b;
+    return MESS_OK;
+}
+
+mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basis** out)
+{
+    if (nmol <= 0 || !bases || !out) { mess_set_error("bad batch arguments"); return MESS_EINVAL; }
+    mess_basis* b = new (std::nothrow) mess_basis();
+    if (!b) { mess_set_error("host allocation failed"); return MESS_ENOMEM; }
+    for (int m = 0; m < nmol; ++m) {
+        const mess_basis* s = bases[m];
+        if (!s || s->nmol != 1) { delete b; mess_set_error("batch entry %d is not a single-molecule basis", m); return MESS_EINVAL; }
+        add_molecule(b, s->Z, s->xyz, s->shells);
+    }
+    mess_status st = build_pairs(b);
+    if (st == MESS_OK) st = build_schwarz(b);
+    if (st != MESS_OK) { mess_free_basis(b); delete b; return st; }
     *out = b;
     return MESS_OK;
 }
@@ -482,7 +568,7 @@ extern "C" int mess_basis_nelectron(const mess_basis* b) { return b ? b->nelec :
 extern "C" void mess_basis_destroy(mess_basis* b)
 {
     if (!b) return;
-    free_basis(b);
+    mess_free_basis(b);
     delete b;
 }
 
@@ -586,7 +672,7 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
     }
     cudaStream_t s = (cudaStream_t)o.cuda_stream;
     const int n = b->nbf;
-    const size_t bytes = (size_t)n * n * sizeof(double);
+    const size_t bytes = (size_t)b->packed * sizeof(double);
     MESS_CUDA_TRY(cudaMemsetAsync(dJ, 0, bytes, s));
     MESS_CUDA_TRY(cudaMemsetAsync(dK, 0, bytes, s));
     std::vector<cudaEvent_t> ev;
@@ -652,7 +738,7 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
         }
     }
     if (out == MESS_OK) {
-        cudaError_t e = mess_launch_symmetrise_jk(dJ, dK, n, s);
+        cudaError_t e = mess_launch_symmetrise_jk(b, dJ, dK, s);
         if (e != cudaSuccess) { mess_set_error("symmetrise: %s", cudaGetErrorString(e)); out = MESS_ECUDA; }
         inf.kernel_launches += 1;
     }
@@ -687,6 +773,12 @@ extern "C" mess_status mess_jk_build_device(const mess_basis* bc, const double* 
                                             const mess_jk_opts* opts, mess_jk_info* info)
 {
     return jk_run(const_cast<mess_basis*>(bc), dD, dJ, dK, opts, info, nullptr, 0, nullptr);
+}
+
+mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
+                           mess_jk_info* info)
+{
+    return jk_run(b, dD, dJ, dK, opts, info, nullptr, 0, nullptr);
 }
 
 extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, double* dJ, double* dK,

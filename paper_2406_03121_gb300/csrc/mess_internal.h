@@ -47,7 +47,9 @@ template <typename T> struct DevBuf {
 };
 
 struct HostShell {
-    int l, K, atom, f0;
+    int l, K, atom, f0;    // f0: global first function (across the molecules of a batch)
+    int fl;                // first function within its molecule
+    int mol;               // molecule index
     double R[3];
     std::vector<double> alpha, coef;   // coef: contraction x primitive norm (x^l component) x contraction norm
 };
@@ -68,23 +70,35 @@ struct BinPart {
 struct BinSet {
     double tau = -1.0, tau64 = -1.0;
     int split = -1;        // whether an FP64 / FP32 split was requested
+    long long active_version = -1;
     std::vector<BinPart> parts;
     DevBuf<int> bra, kbeg;
     DevBuf<long long> offs;
 };
 
+// A basis of one molecule, or (internally) of a batch of molecules: shells, pairs and quartets
+// never couple two molecules, and every n x n matrix of a molecule m is the block
+// [mol_base[m], mol_base[m] + n_m^2) of a packed array (row-major, row stride n_m).
 struct mess_basis {
-    int natom = 0, nbf = 0, nelec = 0;
+    int natom = 0, nbf = 0, nelec = 0;     // totals over the molecules
+    int nmol = 1, max_nbf = 0;
+    long long packed = 0;                   // sum over molecules of n_m^2
     std::vector<int> Z;
     std::vector<double> xyz;
     std::vector<HostShell> shells;
     std::vector<double> fscale;     // per function: component normalisation relative to x^l
+    std::vector<int> f_local;       // per function: index within its molecule
+    std::vector<int> mol_nbf, mol_nelec, mol_atom_off, mol_atom_n, mol_shell_off, mol_shell_n;
+    std::vector<long long> mol_base;
+    std::vector<unsigned char> active;      // per molecule: included in J/K builds
+    long long active_version = 0;
 
-    // canonical shell pairs (A, B): l_A > l_B, or l_A == l_B and A >= B
+    // canonical shell pairs (A, B) within a molecule: l_A > l_B, or l_A == l_B and A >= B
     int npair = 0;
-    std::vector<int> pair_a, pair_b, pair_class, pp_off, pp_n;
+    std::vector<int> pair_a, pair_b, pair_class, pp_off, pp_n, pair_mol;
     std::vector<double> Q;          // Schwarz factor per pair
-    std::vector<int> class_list[MESS_NUM_PCLASS];   // pair ids sorted by Q descending
+    std::vector<int> class_list[MESS_NUM_PCLASS];   // pair ids, per molecule sorted by Q descending
+    std::vector<int> class_seg[MESS_NUM_PCLASS];    // nmol + 1 segment offsets into class_list
     DevBuf<int> d_class_list[MESS_NUM_PCLASS];
 
     DevBuf<PrimPairRec<double>> d_pp64;
@@ -97,7 +111,8 @@ struct mess_basis {
     DevBuf<double> d_xyz;
     DevBuf<int> d_shell_l, d_shell_K, d_shell_f0, d_shell_poff;
     DevBuf<double> d_shell_R, d_shell_alpha, d_shell_coef, d_fscale;
-    DevBuf<int> d_pair_a, d_pair_b;
+    DevBuf<int> d_pair_a, d_pair_b, d_pair_mol, d_mol_n, d_mol_atom_off, d_mol_atom_n, d_f_local;
+    DevBuf<long long> d_mol_base;
 
     PairTable<double> P64;
     PairTable<float> P32;
@@ -107,8 +122,14 @@ struct mess_basis {
 // one-electron integrals on the device (one_e.cu)
 cudaError_t mess_launch_one_e(const mess_basis* b, double* dS, double* dT, double* dV, cudaStream_t s);
 // J/K helpers (jk.cu)
-cudaError_t mess_launch_symmetrise_jk(double* J, double* K, int n, cudaStream_t s);
+cudaError_t mess_launch_symmetrise_jk(const mess_basis* b, double* J, double* K, cudaStream_t s);
 // Boys tables (boys_table.cu): rows x MESS_BOYS_NCOL
 void mess_boys_table(std::vector<double>& tab);
 // bins (host.cu)
 mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split);
+// batches (host.cu): one basis over several molecules (copies of the given bases' shells)
+mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basis** out);
+void mess_free_basis(mess_basis* b);
+// J/K on packed device matrices of (possibly batched) bases (host.cu)
+mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
+                           mess_jk_info* info);

@@ -47,7 +47,12 @@ struct ShellArgs {
     const double *R, *alpha, *coef, *fscale;
     const int* Z;
     const double* xyz;
-    int natom;
+    const int* pair_mol;          // molecule of each pair
+    const int* atom_off;          // [nmol] first atom of the molecule
+    const int* atom_n;            // [nmol] atoms of the molecule
+    const long long* mbase;       // [nmol] offset of the molecule's block in the packed matrices
+    const int* mn;                // [nmol] basis functions of the molecule
+    const int* fglob;             // [nbf] global function index -> offset within its molecule's basis
     const double* boys;
 };
 
@@ -98,7 +103,8 @@ __global__ void k_one_e(const int* __restrict__ pa, const int* __restrict__ pb, 
             double Ve[NCE];
             for (int k = 0; k < NCE; ++k) Ve[k] = 0.0;
             const int Lab = la + lb;
-            for (int C = 0; C < s.natom; ++C) {
+            const int mol = s.pair_mol[t];
+            for (int C = s.atom_off[mol]; C < s.atom_off[mol] + s.atom_n[mol]; ++C) {
                 const double PC[3] = {P[0] - s.xyz[3 * C], P[1] - s.xyz[3 * C + 1], P[2] - s.xyz[3 * C + 2]};
                 double F[LAB + 1];
                 boys_f64_all(Lab, p * (PC[0] * PC[0] + PC[1] * PC[1] + PC[2] * PC[2]), F, s.boys);
@@ -172,11 +178,16 @@ __global__ void k_one_e(const int* __restrict__ pa, const int* __restrict__ pb, 
                 }
         }
     }
-    const int fa = s.f0[A], fb = s.f0[B];
+    const int fa = s.f0[A], fb = s.f0[B];       // global function indices (fscale)
+    const int mol = s.pair_mol[t];
+    const int nm = s.mn[mol];
+    const long long base = s.mbase[mol];
+    const int la0 = s.fglob[fa], lb0 = s.fglob[fb];   // offsets within the molecule
+    (void)n;
     for (int i = 0; i < na; ++i)
         for (int j = 0; j < nb; ++j) {
             const double sc = s.fscale[fa + i] * s.fscale[fb + j];
-            const size_t ij = (size_t)(fa + i) * n + fb + j, ji = (size_t)(fb + j) * n + fa + i;
+            const size_t ij = base + (size_t)(la0 + i) * nm + lb0 + j, ji = base + (size_t)(lb0 + j) * nm + la0 + i;
             if (S) { S[ij] = sc * Sab[i][j]; S[ji] = sc * Sab[i][j]; }
             if (T) { T[ij] = sc * Tab[i][j]; T[ji] = sc * Tab[i][j]; }
             if (V) { V[ij] = sc * Vab[i][j]; V[ji] = sc * Vab[i][j]; }
@@ -190,7 +201,9 @@ cudaError_t mess_launch_one_e(const mess_basis* b, double* dS, double* dT, doubl
     ShellArgs s;
     s.l = b->d_shell_l.p; s.K = b->d_shell_K.p; s.f0 = b->d_shell_f0.p; s.poff = b->d_shell_poff.p;
     s.R = b->d_shell_R.p; s.alpha = b->d_shell_alpha.p; s.coef = b->d_shell_coef.p; s.fscale = b->d_fscale.p;
-    s.Z = b->d_Z.p; s.xyz = b->d_xyz.p; s.natom = b->natom; s.boys = b->d_boys64.p;
+    s.Z = b->d_Z.p; s.xyz = b->d_xyz.p; s.boys = b->d_boys64.p;
+    s.pair_mol = b->d_pair_mol.p; s.atom_off = b->d_mol_atom_off.p; s.atom_n = b->d_mol_atom_n.p;
+    s.mbase = b->d_mol_base.p; s.mn = b->d_mol_n.p; s.fglob = b->d_f_local.p;
     const int T = 64;
     k_one_e<<<(b->npair + T - 1) / T, T, 0, st>>>(b->d_pair_a.p, b->d_pair_b.p, b->npair, s, dS, dT, dV, b->nbf);
     return cudaGetLastError();
