@@ -133,6 +133,21 @@ mess_status mess_jk_build(const mess_basis* b, const double* D, double* J, doubl
 mess_status mess_jk_build_device(const mess_basis* b, const double* dD, double* dJ, double* dK,
                                  const mess_jk_opts* opts, mess_jk_info* info);
 
+/* mess_jk_build without any device allocation (the paper has no counterpart: this is a library
+ * service).  For callers that cannot let a library call cudaMalloc / cudaFree: programs whose
+ * device memory belongs to their own pool or arena, latency-critical loops that cannot absorb
+ * cudaFree's implicit synchronisation, processes running with the device already full.  D, J, K
+ * are staged in one fixed device array inside the library (3 x 256 x 256 doubles, 1.5 MiB per GPU,
+ * held until the process exits) instead of freshly allocated buffers; results equal mess_jk_build's.
+ * Limits: single-molecule bases with n <= 256 (larger n: MESS_EINVAL with a message); the quartet
+ * bins for these opts must already exist - a prior mess_jk_build / mess_jk_build_device call with
+ * the same opts builds them, otherwise MESS_EINVAL.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current), so make that first call
+ * before any stream capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU race on it - serialise them. */
+mess_status mess_jk_build_static(const mess_basis* b, const double* D, double* J, double* K,
+                                 const mess_jk_opts* opts, mess_jk_info* info);
+
 /* Every repulsion integral (mn|ls) in FP64 as a dense n^4 host tensor (index ((m*n+n')*n+l)*n+s).
  * For small bases only (n <= 64).  Errors: MESS_EINVAL (n > 64), MESS_ENOMEM, MESS_ECUDA. */
 mess_status mess_eri_tensor(const mess_basis* b, double* G);

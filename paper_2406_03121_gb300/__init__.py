@@ -28,7 +28,7 @@ PRECISION = {"fp64": MESS_FP64, "mixed": MESS_MIXED, "fp32": MESS_FP32}
 EXPORTED = [
     "mess_basis_create", "mess_basis_nbf", "mess_basis_nshell", "mess_basis_nelectron",
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
-    "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_eri_tensor",
+    "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
     "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_fma_peak", "mess_last_error",
 ]
 
@@ -99,6 +99,8 @@ mess_jk_build = _sig("mess_jk_build", ctypes.c_int,
                      [_P, _DP, _DP, _DP, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_info)])
 mess_jk_build_device = _sig("mess_jk_build_device", ctypes.c_int,
                             [_P, _P, _P, _P, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_info)])
+mess_jk_build_static = _sig("mess_jk_build_static", ctypes.c_int,
+                            [_P, _DP, _DP, _DP, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_info)])
 mess_eri_tensor = _sig("mess_eri_tensor", ctypes.c_int, [_P, _DP])
 mess_schwarz = _sig("mess_schwarz", ctypes.c_int, [_P, _DP])
 mess_scf = _sig("mess_scf", ctypes.c_int,

@@ -781,6 +781,19 @@ mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* 
     return jk_run(b, dD, dJ, dK, opts, info, nullptr, 0, nullptr);
 }
 
+bool mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts)
+{
+    mess_jk_opts o{};
+    if (opts) o = *opts;
+    double tau64 = o.fp64_tau == 0.0 ? MESS_DEFAULT_FP64_TAU : o.fp64_tau;
+    int split = 0;
+    if (o.prec == MESS_MIXED) split = tau64 > 0.0 ? 2 : 1;
+    else if (o.prec == MESS_FP32) split = 1;
+    if (split != 2) tau64 = 0.0;
+    const BinSet& B = b->bins;
+    return B.tau == o.schwarz_tau && B.tau64 == tau64 && B.split == split && B.active_version == b->active_version;
+}
+
 extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, double* dJ, double* dK,
                                        const mess_jk_opts* opts, mess_jk_part* parts, int max_parts, int* nparts)
 {

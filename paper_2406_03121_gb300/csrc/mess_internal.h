@@ -130,6 +130,8 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
 // batches (host.cu): one basis over several molecules (copies of the given bases' shells)
 mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basis** out);
 void mess_free_basis(mess_basis* b);
+// whether the quartet bins for these options are built (a J/K build with them would not allocate)
+bool mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts);
 // J/K on packed device matrices of (possibly batched) bases (host.cu)
 mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
                            mess_jk_info* info);
