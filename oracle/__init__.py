@@ -96,7 +96,7 @@ def num_threads() -> int:
 
 # ----------------------------------------------------------------------------- Boys function
 def boys(nmax: int, T: float) -> np.ndarray:
-    """F_n(T) for n = 0..nmax (series in long double / erf + upward recursion)."""
+    """F_n(T) for n = 0..nmax (compensated positive series / erf + upward recursion)."""
     out = np.zeros(nmax + 1)
     lib().oracle_boys(int(nmax), float(T), _d(out))
     return out

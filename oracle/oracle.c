@@ -33,22 +33,26 @@
 /* ------------------------------------------------------------------------------------------ */
 /* Boys function F_n(T) = int_0^1 t^{2n} exp(-T t^2) dt.                                        */
 /* T < 50: the positive series F_n(T) = exp(-T) sum_i (2T)^i / ((2n+1)(2n+3)...(2n+2i+1)),      */
-/* summed in long double; T >= 50: F_0 from erf and the upward recursion                          */
+/* summed in double with Kahan compensation (every term is positive, so the compensated sum is   */
+/* accurate to a few units in the last place); T >= 50: F_0 from erf and the upward recursion     */
 /* F_{n+1} = ((2n+1) F_n - exp(-T)) / (2T), which is stable for large T.                          */
 /* ------------------------------------------------------------------------------------------ */
 void oracle_boys(int nmax, double T, double *F)
 {
     if (T < 50.0) {
-        long double eT = expl(-(long double)T);
+        double eT = exp(-T);
         for (int n = 0; n <= nmax; ++n) {
-            long double term = 1.0L / (long double)(2 * n + 1);
-            long double sum = term;
+            double term = 1.0 / (double)(2 * n + 1);
+            double sum = term, comp = 0.0;
             for (int i = 1; i < 4000; ++i) {
-                term *= 2.0L * (long double)T / (long double)(2 * n + 2 * i + 1);
-                sum += term;
-                if (term < 1e-22L * sum) break;
+                term *= 2.0 * T / (double)(2 * n + 2 * i + 1);
+                double y = term - comp;
+                double t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+                if (term < 1e-20 * sum) break;
             }
-            F[n] = (double)(eT * sum);
+            F[n] = eT * sum;
         }
     } else {
         double e = exp(-T);
