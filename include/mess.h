@@ -74,6 +74,9 @@ typedef struct {
     long long kernel_launches;       /* kernels launched by the call */
 } mess_jk_info;
 
+/* Initial density of the SCF: eigenvectors of the core Hamiltonian; superposition of spherically
+ * averaged atomic densities (an SCF of each element's atom with fractional 2p occupation); or the
+ * learned guess (mess_mlp_* below).  The converged energy does not depend on the choice. */
 typedef enum { MESS_GUESS_CORE = 0, MESS_GUESS_SAD = 1, MESS_GUESS_MLP = 2 } mess_guess;
 
 typedef struct {
@@ -86,7 +89,7 @@ typedef struct {
     double schwarz_tau;   /* screening threshold for the J/K builds */
     double fp64_tau;      /* MESS_MIXED split, see mess_jk_opts */
     int boys_fp64;        /* see mess_jk_opts */
-    const char* mlp_weights; /* MESS_GUESS_MLP: weight file (unused otherwise) */
+    const char* mlp_weights; /* MESS_GUESS_MLP: weight file of mess_mlp_save (unused otherwise) */
     void* cuda_stream;
 } mess_scf_opts;
 
@@ -193,6 +196,46 @@ mess_status mess_jk_profile(const mess_basis* b, const double* dD, double* dJ, d
  * TFLOP/s (2 flops per FMA), FP32 and FP64, from independent FMA chains timed with CUDA events on
  * cuda_stream.  Used as the roofline denominator of the ALU-bound integral kernels. */
 mess_status mess_fma_peak(double* fp32_tflops, double* fp64_tflops, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned initial density (spec extension; the paper motivates combining ML models with the
+ * SCF, Sec. 1 and its use of Adam, Sec. 5).  A multilayer perceptron 112 -> 256 -> 256 -> 25 (SiLU)
+ * maps descriptors of an ordered atom pair (element one-hots, a Gaussian radial basis of the pair
+ * distance, radial environments of both atoms) to the 5 x 5 density block of the pair in a frame
+ * with z along the pair axis (minimal basis: 1 function on H, s s' p on C / N / O, e.g. STO-3G).
+ * BF16 inputs and weights, FP32 accumulation on tensor cores, FP32 master weights, Adam.
+ * Parameter vector layout (floats): W1[112][256], b1[256], W2[256][256], b2[256], W3[256][32]
+ * (columns 25..31 unused), b3[32].
+ * ------------------------------------------------------------------------------------------- */
+#define MESS_MLP_DIN 112
+#define MESS_MLP_WIDTH 256
+#define MESS_MLP_DOUT 25
+typedef struct mess_mlp mess_mlp;   /* opaque, library-owned */
+
+int mess_mlp_num_params(void);
+/* New network with weights uniform in +-1/sqrt(fan_in) from a seeded splitmix64 stream, zero biases. */
+mess_status mess_mlp_create(unsigned long long seed, mess_mlp** out);
+void mess_mlp_destroy(mess_mlp* m);
+mess_status mess_mlp_get_params(const mess_mlp* m, float* params /* mess_mlp_num_params() */);
+mess_status mess_mlp_set_params(mess_mlp* m, const float* params);
+/* Binary weight file: "MESSMLP1", 4 ints (112, 256, 25, num_params), the FP32 parameters. */
+mess_status mess_mlp_save(const mess_mlp* m, const char* path);
+mess_status mess_mlp_load(const char* path, mess_mlp** out);
+/* Descriptors of all ordered atom pairs of one molecule (rows = natom^2, row i*natom + j), and with a
+ * density D (host n*n) the pair-frame targets T and masks M (rows x 25).  X/T/M may be NULL to query
+ * *nrows only.  Errors: MESS_EINVAL for a basis that is not minimal (see above). */
+mess_status mess_mlp_features(const mess_basis* b, const double* D, float* X, float* T, float* M, long long* nrows);
+/* One forward + backward pass over host rows: masked mean squared error and its gradient
+ * (mess_mlp_num_params() floats).  For gradient checks. */
+mess_status mess_mlp_loss_grad(mess_mlp* m, long long nrows, const float* X, const float* T, const float* M,
+                               double* loss, float* grad);
+/* Train on the converged densities of bases[0..nmol) (batched device SCF with opts scf), every
+ * ordered atom pair one row, Adam (lr, beta 0.9 / 0.999) over shuffled batches of batch_rows rows for
+ * `epochs` epochs; loss_out (nullable, epochs doubles) receives each epoch's mean loss. */
+mess_status mess_mlp_train(mess_mlp* m, int nmol, mess_basis* const* bases, const mess_scf_opts* scf, int epochs,
+                           int batch_rows, double lr, double* loss_out);
+/* The network's density D0 (host n*n, symmetrised, before any diagonalisation) for one molecule. */
+mess_status mess_mlp_predict(const mess_mlp* m, const mess_basis* b, double* D0);
 
 /* Message for the calling thread's most recent failure ("" if none).  Valid until the next call. */
 const char* mess_last_error(void);

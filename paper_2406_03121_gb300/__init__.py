@@ -30,7 +30,11 @@ EXPORTED = [
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
     "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
     "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_fma_peak", "mess_last_error",
+    "mess_mlp_num_params", "mess_mlp_create", "mess_mlp_destroy", "mess_mlp_get_params", "mess_mlp_set_params",
+    "mess_mlp_save", "mess_mlp_load", "mess_mlp_features", "mess_mlp_loss_grad", "mess_mlp_train",
+    "mess_mlp_predict",
 ]
+MLP_DIN, MLP_WIDTH, MLP_DOUT = 112, 256, 25
 
 
 class mess_jk_opts(ctypes.Structure):
@@ -113,6 +117,22 @@ mess_jk_profile = _sig("mess_jk_profile", ctypes.c_int,
                         ctypes.POINTER(ctypes.c_int)])
 mess_fma_peak = _sig("mess_fma_peak", ctypes.c_int, [_DP, _DP, _P])
 mess_last_error = _sig("mess_last_error", ctypes.c_char_p, [])
+_FP = ctypes.POINTER(ctypes.c_float)
+mess_mlp_num_params = _sig("mess_mlp_num_params", ctypes.c_int, [])
+mess_mlp_create = _sig("mess_mlp_create", ctypes.c_int, [ctypes.c_ulonglong, ctypes.POINTER(_P)])
+mess_mlp_destroy = _sig("mess_mlp_destroy", None, [_P])
+mess_mlp_get_params = _sig("mess_mlp_get_params", ctypes.c_int, [_P, _FP])
+mess_mlp_set_params = _sig("mess_mlp_set_params", ctypes.c_int, [_P, _FP])
+mess_mlp_save = _sig("mess_mlp_save", ctypes.c_int, [_P, ctypes.c_char_p])
+mess_mlp_load = _sig("mess_mlp_load", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_P)])
+mess_mlp_features = _sig("mess_mlp_features", ctypes.c_int,
+                         [_P, _DP, _FP, _FP, _FP, ctypes.POINTER(ctypes.c_longlong)])
+mess_mlp_loss_grad = _sig("mess_mlp_loss_grad", ctypes.c_int,
+                          [_P, ctypes.c_longlong, _FP, _FP, _FP, _DP, _FP])
+mess_mlp_train = _sig("mess_mlp_train", ctypes.c_int,
+                      [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(mess_scf_opts), ctypes.c_int, ctypes.c_int,
+                       ctypes.c_double, _DP])
+mess_mlp_predict = _sig("mess_mlp_predict", ctypes.c_int, [_P, _P, _DP])
 
 
 class MessError(RuntimeError):
@@ -295,3 +315,88 @@ def scf_batch(bases, prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e
     if st not in (MESS_OK, MESS_ENOCONV):
         _check(st, "mess_scf_batch")
     return [r.as_dict() for r in res], st
+
+
+def _fptr(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_FP)
+
+
+class MLP:
+    """The learned-guess network (owns a ``mess_mlp``)."""
+
+    def __init__(self, seed: int = 1, path: str | None = None):
+        h = _P()
+        if path is None:
+            _check(mess_mlp_create(ctypes.c_ulonglong(seed), ctypes.byref(h)), "mess_mlp_create")
+        else:
+            _check(mess_mlp_load(os.fsencode(path), ctypes.byref(h)), "mess_mlp_load")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            mess_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def num_params() -> int:
+        return int(mess_mlp_num_params())
+
+    def get_params(self):
+        out = np.zeros(self.num_params(), dtype=np.float32)
+        _check(mess_mlp_get_params(self._h, _fptr(out)), "mess_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(mess_mlp_set_params(self._h, _fptr(p)), "mess_mlp_set_params")
+
+    def save(self, path):
+        _check(mess_mlp_save(self._h, os.fsencode(path)), "mess_mlp_save")
+
+    def loss_grad(self, X, T, M):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        M = np.ascontiguousarray(M, dtype=np.float32)
+        loss = ctypes.c_double()
+        g = np.zeros(self.num_params(), dtype=np.float32)
+        _check(mess_mlp_loss_grad(self._h, X.shape[0], _fptr(X), _fptr(T), _fptr(M), ctypes.byref(loss), _fptr(g)),
+               "mess_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, bases, epochs=10, batch_rows=8192, lr=1e-3, **scf_kw):
+        n = len(bases)
+        arr = (_P * n)(*[b.handle for b in bases])
+        o = scf_opts(**scf_kw)
+        losses = np.zeros(epochs)
+        _check(mess_mlp_train(self._h, n, arr, ctypes.byref(o), epochs, batch_rows, lr, _dptr(losses)),
+               "mess_mlp_train")
+        return losses
+
+    def predict(self, basis):
+        D0 = np.zeros((basis.nbf, basis.nbf))
+        _check(mess_mlp_predict(self._h, basis.handle, _dptr(D0)), "mess_mlp_predict")
+        return D0
+
+
+def mlp_features(basis, D=None):
+    """(X, T, M) descriptors / pair-frame targets / masks of one molecule (T, M None without D)."""
+    n = ctypes.c_longlong()
+    _check(mess_mlp_features(basis.handle, None, None, None, None, ctypes.byref(n)), "mess_mlp_features")
+    rows = n.value
+    X = np.zeros((rows, MLP_DIN), dtype=np.float32)
+    if D is None:
+        _check(mess_mlp_features(basis.handle, None, _fptr(X), None, None, ctypes.byref(n)), "mess_mlp_features")
+        return X, None, None
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    T = np.zeros((rows, MLP_DOUT), dtype=np.float32)
+    M = np.zeros((rows, MLP_DOUT), dtype=np.float32)
+    _check(mess_mlp_features(basis.handle, _dptr(D), _fptr(X), _fptr(T), _fptr(M), ctypes.byref(n)),
+           "mess_mlp_features")
+    return X, T, M

@@ -544,6 +544,32 @@ extern "C" mess_status mess_basis_create(int natom, const int* Z, const double* 
     return MESS_OK;
 }
 
+mess_status mess_atoms_basis(const mess_basis* b, std::vector<int>& elements, mess_basis** out)
+{
+    elements.clear();
+    mess_basis* a = new (std::nothrow) mess_basis();
+    if (!a) { mess_set_error("host allocation failed"); return MESS_ENOMEM; }
+    for (int at = 0; at < b->natom; ++at) {
+        const int z = b->Z[at];
+        if (std::find(elements.begin(), elements.end(), z) != elements.end()) continue;
+        elements.push_back(z);
+        std::vector<HostShell> sh;
+        for (const HostShell& s : b->shells)
+            if (s.atom == at) {
+                HostShell c = s;
+                c.atom = 0;
+                c.R[0] = c.R[1] = c.R[2] = 0.0;
+                sh.push_back(c);
+            }
+        add_molecule(a, std::vector<int>{z}, std::vector<double>{0.0, 0.0, 0.0}, sh);
+    }
+    mess_status st = build_pairs(a);
+    if (st == MESS_OK) st = build_schwarz(a);
+    if (st != MESS_OK) { mess_free_basis(a); delete a; return st; }
+    *out = a;
+    return MESS_OK;
+}
+
 mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basis** out)
 {
     if (nmol <= 0 || !bases || !out) { mess_set_error("bad batch arguments"); return MESS_EINVAL; }

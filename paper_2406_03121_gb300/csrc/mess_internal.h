@@ -130,6 +130,12 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
 // batches (host.cu): one basis over several molecules (copies of the given bases' shells)
 mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basis** out);
 void mess_free_basis(mess_basis* b);
+// one single-atom molecule (at the origin) per distinct element of b; elements[e] = Z of molecule e
+mess_status mess_atoms_basis(const mess_basis* b, std::vector<int>& elements, mess_basis** out);
+// batched SCF on an internal batch basis, final densities into dD (device, packed) (scf.cu)
+mess_status mess_scf_batch_density(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* dD);
+// learned guess: predicted D0 of every molecule of b (device, packed) (mlp.cu)
+mess_status mess_mlp_guess_device(const mess_mlp* m, const mess_basis* b, double* dD0, cudaStream_t s);
 // whether the quartet bins for these options are built (a J/K build with them would not allocate)
 bool mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts);
 // J/K on packed device matrices of (possibly batched) bases (host.cu)

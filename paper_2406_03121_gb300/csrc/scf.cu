@@ -20,8 +20,10 @@ namespace {
 struct Layout {
     const long long* base;   // [nmol]
     const int* n;            // [nmol]
-    const int* nocc;         // [nmol]
+    const int* nocc;         // [nmol] orbitals with a non-zero occupation
     const unsigned char* active;   // [nmol]
+    const double* occ;       // occupation of orbital k of molecule m at occ[obase[m] + k] (energy order)
+    const long long* obase;  // [nmol]
 };
 
 __device__ __forceinline__ double block_sum(double v, double* red)
@@ -92,7 +94,8 @@ __global__ void k_energy(const double* __restrict__ D, const double* __restrict_
 }
 
 // C = alpha * A op(B) + beta * C per molecule; A is n x k (row stride n), op(B) k x n; k = n (kmode 0)
-// or nocc (kmode 1).  16 x 16 output tiles staged through shared memory.
+// or the occupied orbitals (kmode 1, column kk of A weighted by its occupation: C diag(occ) C^T).
+// 16 x 16 output tiles staged through shared memory.
 template <bool TRANSA, bool TRANSB>
 __global__ void k_gemm(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
                        Layout L, int kmode, double alpha, double beta)
@@ -113,7 +116,9 @@ __global__ void k_gemm(const double* __restrict__ A, const double* __restrict__ 
             As[tx][ty] = (ar < k && ac < n) ? A[o + (long long)ar * n + ac] : 0.0;
         } else {
             const int ar = r0 + ty, ac = k0 + tx;
-            As[ty][tx] = (ar < n && ac < k) ? A[o + (long long)ar * n + ac] : 0.0;
+            double w = 1.0;
+            if (kmode && ac < k) w = L.occ[L.obase[m] + ac];
+            As[ty][tx] = (ar < n && ac < k) ? w * A[o + (long long)ar * n + ac] : 0.0;
         }
         if (TRANSB) {
             const int br = c0 + ty, bc = k0 + tx;      // B[j][kk]
@@ -360,6 +365,7 @@ struct SCFState {
     Dev<double> Vprev, Dprev, Jt, Kt;   // warm-start eigenvectors, previous density, accumulated J / K
     bool warm = false;
     Dev<long long> base, ebase;
+    Dev<double> occ;
     Dev<int> n, nocc, sweeps;
     Dev<unsigned char> active;
     int use_smem;
@@ -379,6 +385,11 @@ cudaError_t gemm(SCFState& st, bool transB, const double* A, const double* B, do
 
 cudaError_t jacobi(SCFState& st, const double* A, double* Vout)
 {
+    // the attribute is per kernel, not per call: a nested SCF (atomic densities) may have lowered it
+    if (st.use_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st.jac_smem);
+        if (e != cudaSuccess) return e;
+    }
     k_jacobi<<<st.nmol, 512, st.jac_smem, st.s>>>(A, st.W2.p, Vout, st.eps.p, st.ebase.p, st.L, st.use_smem,
                                                   st.Wk.p, 40, st.sweeps.p);
     return cudaGetLastError();
@@ -404,10 +415,95 @@ cudaError_t density_from_fock(SCFState& st, const double* Fin)
     }
     if ((e = cudaMemcpyAsync(st.Vprev.p, st.V.p, sizeof(double) * st.P, cudaMemcpyDeviceToDevice, st.s)) != cudaSuccess) return e;
     if ((e = gemm(st, false, st.X.p, st.V.p, st.C.p, 0, 1.0)) != cudaSuccess) return e;  // C = X V
-    return gemm(st, true, st.C.p, st.C.p, st.D.p, 1, 2.0);                             // D = 2 C_occ C_occ^T
+    return gemm(st, true, st.C.p, st.C.p, st.D.p, 1, 1.0);                             // D = C diag(occ) C^T
 }
 
-mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* D_out, bool D_out_device)
+// Block-diagonal superposition of atomic densities: atom a of molecule m (functions [f, f + na) of
+// the molecule) receives the density block of its element (molecule e of the atomic batch).
+__global__ void k_assemble_blocks(double* __restrict__ D, const long long* __restrict__ mbase, const int* __restrict__ mn,
+                                  const int* __restrict__ amol, const int* __restrict__ af, const int* __restrict__ an,
+                                  const int* __restrict__ ael, const double* __restrict__ Dat,
+                                  const long long* __restrict__ ebase, int natom)
+{
+    const int a = blockIdx.x;
+    if (a >= natom) return;
+    const int m = amol[a], f = af[a], na = an[a];
+    const long long o = mbase[m], eo = ebase[ael[a]];
+    const int n = mn[m];
+    for (int t = threadIdx.x; t < na * na; t += blockDim.x) {
+        const int i = t / na, j = t % na;
+        D[o + (long long)(f + i) * n + f + j] = Dat[eo + (long long)i * na + j];
+    }
+}
+
+// occupations of the orbitals (energy order) of one neutral atom, spherically averaged: 1s, 2s
+// doubly occupied, the 2p electrons spread evenly over the three 2p orbitals (reading C10)
+static std::vector<double> atomic_occupation(int Z)
+{
+    std::vector<double> o;
+    if (Z <= 2) { o.push_back((double)Z); return o; }
+    o.push_back(2.0);
+    if (Z <= 4) { o.push_back((double)(Z - 2)); return o; }
+    o.push_back(2.0);
+    for (int k = 0; k < 3; ++k) o.push_back((Z - 4) / 3.0);
+    return o;
+}
+
+mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* D_out, bool D_out_device,
+                    const std::vector<std::vector<double>>* occ_in = nullptr);
+
+// Superposition of atomic densities: an SCF of every distinct element as an isolated atom with
+// spherically averaged fractional occupation, then the block-diagonal D0 of each molecule.
+static mess_status sad_density(mess_basis* b, const mess_scf_opts& o, double* D0, cudaStream_t s)
+{
+    std::vector<int> elements;
+    mess_basis* atoms = nullptr;
+    mess_status st = mess_atoms_basis(b, elements, &atoms);
+    if (st != MESS_OK) return st;
+    std::vector<std::vector<double>> occ;
+    for (int z : elements) occ.push_back(atomic_occupation(z));
+    mess_scf_opts ao = o;
+    ao.guess = MESS_GUESS_CORE;
+    ao.prec = MESS_FP64;
+    ao.max_iter = 200;
+    std::vector<mess_scf_result> ares(elements.size());
+    DevBuf<double> Dat;
+    cudaError_t e = Dat.alloc((size_t)atoms->packed);
+    if (e != cudaSuccess) { mess_free_basis(atoms); delete atoms; mess_set_error("SAD: allocation failed"); return MESS_ENOMEM; }
+    st = scf_run(atoms, &ao, ares.data(), Dat.p, true, &occ);
+    if (st != MESS_OK && st != MESS_ENOCONV) { Dat.free(); mess_free_basis(atoms); delete atoms; return st; }
+    // per atom of b: molecule, first local function, function count, element index in `elements`
+    std::vector<int> amol(b->natom), af(b->natom, -1), an(b->natom, 0), ael(b->natom);
+    for (const HostShell& sh : b->shells) {
+        if (af[sh.atom] < 0) af[sh.atom] = sh.fl;
+        an[sh.atom] += (sh.l + 1) * (sh.l + 2) / 2;
+        amol[sh.atom] = sh.mol;
+    }
+    for (int a = 0; a < b->natom; ++a)
+        ael[a] = (int)(std::find(elements.begin(), elements.end(), b->Z[a]) - elements.begin());
+    DevBuf<int> d_amol, d_af, d_an, d_ael;
+    if (d_amol.upload(amol) != cudaSuccess || d_af.upload(af) != cudaSuccess || d_an.upload(an) != cudaSuccess ||
+        d_ael.upload(ael) != cudaSuccess) {
+        Dat.free(); mess_free_basis(atoms); delete atoms;
+        mess_set_error("SAD: upload failed");
+        return MESS_ECUDA;
+    }
+    e = cudaMemsetAsync(D0, 0, sizeof(double) * b->packed, s);
+    if (e == cudaSuccess) {
+        k_assemble_blocks<<<b->natom, 128, 0, s>>>(D0, b->d_mol_base.p, b->d_mol_n.p, d_amol.p, d_af.p, d_an.p,
+                                                   d_ael.p, Dat.p, atoms->d_mol_base.p, b->natom);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    Dat.free(); d_amol.free(); d_af.free(); d_an.free(); d_ael.free();
+    mess_free_basis(atoms);
+    delete atoms;
+    if (e != cudaSuccess) { mess_set_error("SAD assembly: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
+    return MESS_OK;
+}
+
+mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* D_out, bool D_out_device,
+                    const std::vector<std::vector<double>>* occ_in)
 {
     mess_scf_opts o{};
     if (opts) o = *opts;
@@ -415,9 +511,9 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
     const double conv_E = o.conv_E > 0 ? o.conv_E : 1e-10;
     const double conv_comm = o.conv_comm > 0 ? o.conv_comm : 1e-8;
     const int diis_n = std::min(o.diis_n > 0 ? o.diis_n : 8, 16);
-    if (o.guess != MESS_GUESS_CORE) {
-        mess_set_error("mess_scf: only the core-Hamiltonian guess is available in this build");
-        return MESS_ENOTIMPL;
+    if (o.guess != MESS_GUESS_CORE && o.guess != MESS_GUESS_SAD && o.guess != MESS_GUESS_MLP) {
+        mess_set_error("mess_scf: unknown initial guess %d", o.guess);
+        return MESS_EINVAL;
     }
     if (b->max_nbf > 256) {
         mess_set_error("mess_scf: %d basis functions; the on-device eigensolver handles n <= 256", b->max_nbf);
@@ -433,10 +529,24 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
     std::vector<long long> ebase(b->nmol);
     long long etot = 0;
     for (int m = 0; m < b->nmol; ++m) {
-        if (b->mol_nelec[m] % 2) { mess_set_error("molecule %d: odd electron count %d", m, b->mol_nelec[m]); return MESS_EINVAL; }
-        nocc[m] = b->mol_nelec[m] / 2;
+        if (!occ_in && b->mol_nelec[m] % 2) {
+            mess_set_error("molecule %d: odd electron count %d", m, b->mol_nelec[m]);
+            return MESS_EINVAL;
+        }
         ebase[m] = etot;
         etot += b->mol_nbf[m];
+    }
+    std::vector<double> occ_h((size_t)etot, 0.0);
+    for (int m = 0; m < b->nmol; ++m) {
+        if (occ_in) {
+            const std::vector<double>& w = (*occ_in)[m];
+            if ((int)w.size() > b->mol_nbf[m]) { mess_set_error("molecule %d: too many occupied orbitals", m); return MESS_EINVAL; }
+            for (size_t k = 0; k < w.size(); ++k) occ_h[ebase[m] + k] = w[k];
+            nocc[m] = (int)w.size();
+        } else {
+            nocc[m] = b->mol_nelec[m] / 2;
+            for (int k = 0; k < nocc[m]; ++k) occ_h[ebase[m] + k] = 2.0;
+        }
     }
     const size_t P = (size_t)st.P;
     for (Dev<double>* d : {&st.S, &st.H, &st.X, &st.F, &st.D, &st.J, &st.K, &st.V, &st.C, &st.W1, &st.W2, &st.e,
@@ -445,6 +555,8 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
     MESS_CUDA_TRY(st.Fh.alloc(P * diis_n));
     MESS_CUDA_TRY(st.eh.alloc(P * diis_n));
     MESS_CUDA_TRY(st.eps.alloc(etot));
+    MESS_CUDA_TRY(st.occ.alloc(etot));
+    MESS_CUDA_TRY(cudaMemcpy(st.occ.p, occ_h.data(), sizeof(double) * etot, cudaMemcpyHostToDevice));
     MESS_CUDA_TRY(st.E.alloc(b->nmol));
     MESS_CUDA_TRY(st.emax.alloc(b->nmol));
     MESS_CUDA_TRY(st.smin.alloc(b->nmol));
@@ -461,7 +573,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
     MESS_CUDA_TRY(cudaMemcpy(st.nocc.p, nocc.data(), sizeof(int) * b->nmol, cudaMemcpyHostToDevice));
     std::vector<unsigned char> act(b->nmol, 1);
     MESS_CUDA_TRY(cudaMemcpy(st.active.p, act.data(), b->nmol, cudaMemcpyHostToDevice));
-    st.L = Layout{st.base.p, st.n.p, st.nocc.p, st.active.p};
+    st.L = Layout{st.base.p, st.n.p, st.nocc.p, st.active.p, st.occ.p, st.ebase.p};
     // Jacobi matrix in shared memory when it fits
     const size_t need = (size_t)st.maxn * st.maxn * sizeof(double);
     int dev = 0, smax = 0;
@@ -469,8 +581,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
     MESS_CUDA_TRY(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     st.use_smem = need + 4096 <= (size_t)smax - 8192 ? 1 : 0;
     st.jac_smem = st.use_smem ? need : 0;
-    if (st.use_smem) MESS_CUDA_TRY(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-    else MESS_CUDA_TRY(st.Wk.alloc(P));
+    if (!st.use_smem) MESS_CUDA_TRY(st.Wk.alloc(P));
     for (int m = 0; m < b->nmol; ++m) b->active[m] = 1;
     b->active_version++;
 
@@ -489,9 +600,22 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
     for (int m = 0; m < b->nmol; ++m)
         if (!(hmin[m] > 1e-7)) { mess_set_error("molecule %d: overlap matrix nearly singular (%g)", m, hmin[m]); return MESS_ENUMERIC; }
 
-    // core-Hamiltonian guess
+    // initial density: core Hamiltonian (eigenvectors of X H X), or the superposition of atomic densities
     st.warm = false;
-    MESS_CUDA_TRY(density_from_fock(st, st.H.p));
+    if (o.guess == MESS_GUESS_SAD && !occ_in) {
+        mess_status gs = sad_density(b, o, st.D.p, st.s);
+        if (gs != MESS_OK) return gs;
+    } else if (o.guess == MESS_GUESS_MLP && !occ_in) {
+        if (!o.mlp_weights) { mess_set_error("MESS_GUESS_MLP needs opts->mlp_weights"); return MESS_EINVAL; }
+        mess_mlp* net = nullptr;
+        mess_status gs = mess_mlp_load(o.mlp_weights, &net);
+        if (gs != MESS_OK) return gs;
+        gs = mess_mlp_guess_device(net, b, st.D.p, st.s);
+        mess_mlp_destroy(net);
+        if (gs != MESS_OK) return gs;
+    } else {
+        MESS_CUDA_TRY(density_from_fock(st, st.H.p));
+    }
 
     std::vector<double> Enuc(b->nmol), E(b->nmol), Eold(b->nmol, 0.0), em(b->nmol);
     std::vector<int> iters(b->nmol, 0), conv(b->nmol, 0);
@@ -601,6 +725,11 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
 }
 
 }  // namespace
+
+mess_status mess_scf_batch_density(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* dD)
+{
+    return scf_run(b, opts, res, dD, true);
+}
 
 extern "C" mess_status mess_scf(const mess_basis* bc, const mess_scf_opts* opts, mess_scf_result* res, double* D_out)
 {

@@ -75,3 +75,13 @@ def test_scf_errors(mess):
     h2o = mess.Basis.from_molecule(mi.h2o(), mi.basis_path("sto-3g"))
     r = h2o.scf(max_iter=2)
     assert r["status"] == mess.MESS_ENOCONV and r["converged"] == 0
+
+
+def test_sad_guess_same_energy(mess, oracle_mod):
+    for mol, basis in ((mi.h2o(), "6-31gs"), (mi.alkane(4, np.random.default_rng(9)), "sto-3g")):
+        g = mess.Basis.from_molecule(mol, mi.basis_path(basis))
+        rc = g.scf(guess=mess.MESS_GUESS_CORE)
+        rs = g.scf(guess=mess.MESS_GUESS_SAD)
+        assert rc["converged"] == 1 and rs["converged"] == 1
+        assert abs(rs["E_total"] - rc["E_total"]) <= 1e-8
+        assert rs["iterations"] <= rc["iterations"] + 1
