@@ -268,10 +268,10 @@ class Basis:
 
     def jk_profile(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False):
         """Per-launch timings (CUDA events) and algorithmic flops of one device J/K build."""
-        parts = (mess_jk_part * 128)()
+        parts = (mess_jk_part * 1024)()
         n = ctypes.c_int()
         o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64)
-        _check(mess_jk_profile(self._h, _tptr(D), _tptr(J), _tptr(K), ctypes.byref(o), parts, 128, ctypes.byref(n)),
+        _check(mess_jk_profile(self._h, _tptr(D), _tptr(J), _tptr(K), ctypes.byref(o), parts, 1024, ctypes.byref(n)),
                "mess_jk_profile")
         return [parts[i].as_dict() for i in range(n.value)]
 

@@ -15,6 +15,38 @@
 // ------------------------------------------------------------------------------------------
 template <typename R> struct PrimPair { R zeta, Px, Py, Pz, PAx, PAy, PAz, K, oo2z; };
 
+template <typename R> struct PairTable;
+
+// Conversions between FP64 and FP32 done on the integer ALU: on this GPU the FP64 pipe (which also
+// executes F2F conversions) runs at 1/64 of the FP32 rate, so FP32 kernels avoid it entirely.
+// Values outside the normal FP32 range (|x| < 2^-126 becomes 0; infinities / NaN) take the
+// hardware conversion.
+__device__ __forceinline__ float d2f_alu(double d)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(d) + (1ull << 28);   // round to nearest
+    const unsigned hi = (unsigned)(b >> 32);
+    const int fe = (int)((hi >> 20) & 0x7ffu) - 896;
+    if (fe <= 0) return __uint_as_float(hi & 0x80000000u);
+    if (fe >= 255) return (float)d;
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+__device__ __forceinline__ double f2d_alu(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    if (e == 0xffu) return (double)f;
+    const unsigned m = u & 0x7fffffu;
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
+template <typename R> __device__ __forceinline__ R ldD(const double* p);
+template <> __device__ __forceinline__ double ldD<double>(const double* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldD<float>(const double* p) { return d2f_alu(__ldg(p)); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return f2d_alu(v); }
+
 template <typename R> struct PairTable {
     const PrimPairRec<R>* __restrict__ pp;   // [npp]
     const int* __restrict__ pp_off;          // [npair]
@@ -24,6 +56,8 @@ template <typename R> struct PairTable {
     const int* __restrict__ fb;              // [npair] first function of B
     const int* __restrict__ same;            // [npair] 1 if A == B (same shell)
     const double* __restrict__ C;            // [npair][3] centre of the pair's first shell A
+    const float* __restrict__ Cf;            // [npair][6] the same as FP32 hi[3], lo[3] (C = hi + lo)
+    const float* __restrict__ ABf;           // [npair][3] A - B in FP32
     const int* __restrict__ mol;             // [npair] molecule of the pair (batched bases)
     const long long* __restrict__ mbase;     // [nmol] offset of the molecule's n x n block (packed matrices)
     const int* __restrict__ mn;              // [nmol] basis functions of the molecule (row stride)
@@ -40,6 +74,19 @@ template <typename R> struct PairTable {
         return o;
     }
 };
+
+// A - C between the first shells of two pairs, and A - B of one pair, in R.  FP32 forms the
+// difference from hi/lo parts, so it is accurate relative to |A - C|, not to |A|.
+__device__ __forceinline__ double pair_ac(const PairTable<double>& P, int bp, int kp, int x)
+{
+    return P.C[3 * bp + x] - P.C[3 * kp + x];
+}
+__device__ __forceinline__ float pair_ac(const PairTable<float>& P, int bp, int kp, int x)
+{
+    return (__ldg(P.Cf + 6 * bp + x) - __ldg(P.Cf + 6 * kp + x)) + (__ldg(P.Cf + 6 * bp + 3 + x) - __ldg(P.Cf + 6 * kp + 3 + x));
+}
+__device__ __forceinline__ double pair_ab(const PairTable<double>& P, int p, int x) { return P.AB[3 * p + x]; }
+__device__ __forceinline__ float pair_ab(const PairTable<float>& P, int p, int x) { return __ldg(P.ABf + 3 * p + x); }
 
 // ------------------------------------------------------------------------------------------
 // Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt, m = 0..L.
@@ -91,8 +138,11 @@ template <int L> __device__ __forceinline__ void boys_large_f64(double T, double
 
 template <int L> __device__ __forceinline__ void boys_small_f32(float T, float* F, const float* __restrict__ c_boys32)
 {
-    const int k = __float2int_rn(T * (float)MESS_BOYS_INV_DT);
-    const float x = (float)k * (float)MESS_BOYS_DT - T;
+    // nearest grid index without F2I / I2F conversions (those issue on the slow FP64 pipe): adding
+    // 1.5 * 2^23 rounds T / dT to an integer held in the low mantissa bits (0 <= T / dT < 2^22)
+    const float r = fmaf(T, (float)MESS_BOYS_INV_DT, 12582912.0f);
+    const int k = __float_as_int(r) - 0x4B400000;
+    const float x = (r - 12582912.0f) * (float)MESS_BOYS_DT - T;
     const float* row = c_boys32 + (size_t)k * MESS_BOYS_NCOL;
     if (L == 0) {
         float s = __ldg(row + 4);
@@ -207,9 +257,9 @@ __device__ __forceinline__ void jk_add(double* __restrict__ M, size_t idx, R v, 
 {
     if (warp_reduce) {
         v = warp_sum(v);
-        if ((threadIdx.x & 31) == 0) atomicAdd(M + idx, (double)v);
+        if ((threadIdx.x & 31) == 0) atomicAdd(M + idx, to_f64(v));
     } else {
-        if (v != R(0)) atomicAdd(M + idx, (double)v);
+        if (v != R(0)) atomicAdd(M + idx, to_f64(v));
     }
 }
 
@@ -354,8 +404,7 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
     for (int k = 0; k < NACC; ++k) H[k] = R(0);
     const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];
     const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
-    const R ACx = R(P.C[3 * bp] - P.C[3 * kp]), ACy = R(P.C[3 * bp + 1] - P.C[3 * kp + 1]);
-    const R ACz = R(P.C[3 * bp + 2] - P.C[3 * kp + 2]);
+    const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);
 #pragma unroll 1
     for (int ib = b0; ib < b1; ++ib) {
         const PrimPair<R> pb = P.load(ib);
@@ -401,8 +450,8 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
             }
         }
     }
-    const R ABx = R(P.AB[3 * bp]), ABy = R(P.AB[3 * bp + 1]), ABz = R(P.AB[3 * bp + 2]);
-    const R CDx = R(P.AB[3 * kp]), CDy = R(P.AB[3 * kp + 1]), CDz = R(P.AB[3 * kp + 2]);
+    const R ABx = pair_ab(P, bp, 0), ABy = pair_ab(P, bp, 1), ABz = pair_ab(P, bp, 2);
+    const R CDx = pair_ab(P, kp, 0), CDy = pair_ab(P, kp, 1), CDz = pair_ab(P, kp, 2);
 #pragma unroll 1
     for (int o = 0; o < NHOPS; ++o) {
         const uint2 w = __ldg(hprog + o);
@@ -442,8 +491,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     __syncwarp();
     const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];
     const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
-    const R ACx = R(P.C[3 * bp] - P.C[3 * kp]), ACy = R(P.C[3 * bp + 1] - P.C[3 * kp + 1]);
-    const R ACz = R(P.C[3 * bp + 2] - P.C[3 * kp + 2]);
+    const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);
 #pragma unroll 1
     for (int ib = b0; ib < b1; ++ib) {
         const PrimPair<R> pb = P.load(ib);
@@ -492,8 +540,8 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
             }
         }
     }
-    const R ABx = R(P.AB[3 * bp]), ABy = R(P.AB[3 * bp + 1]), ABz = R(P.AB[3 * bp + 2]);
-    const R CDx = R(P.AB[3 * kp]), CDy = R(P.AB[3 * kp + 1]), CDz = R(P.AB[3 * kp + 2]);
+    const R ABx = pair_ab(P, bp, 0), ABy = pair_ab(P, bp, 1), ABz = pair_ab(P, bp, 2);
+    const R CDx = pair_ab(P, kp, 0), CDy = pair_ab(P, kp, 1), CDz = pair_ab(P, kp, 2);
 #pragma unroll 1
     for (int lv = 0; lv < NHL; ++lv) {
         const int oend = __ldg(hlev + lv + 1);
@@ -526,43 +574,43 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
         const int a = o / NB, bb = o % NB;
         R t = R(0);
         for (int c = 0; c < NC; ++c)
-            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fc + c) * nn + fd + d));
-        atomicAdd(J + (fa + a) * nn + fb + bb, (double)(s * t));
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fc + c) * nn + fd + d);
+        atomicAdd(J + (fa + a) * nn + fb + bb, to_f64(s * t));
     }
     for (int o = lane; o < NC * ND; o += 32) {          // J_cd = sum_ab I D_ab
         const int c = o / ND, d = o % ND;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
-            for (int bb = 0; bb < NB; ++bb) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fa + a) * nn + fb + bb));
-        atomicAdd(J + (fc + c) * nn + fd + d, (double)(s * t));
+            for (int bb = 0; bb < NB; ++bb) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fa + a) * nn + fb + bb);
+        atomicAdd(J + (fc + c) * nn + fd + d, to_f64(s * t));
     }
     for (int o = lane; o < NA * NC; o += 32) {          // K_ac = sum_bd I D_bd
         const int a = o / NC, c = o % NC;
         R t = R(0);
         for (int bb = 0; bb < NB; ++bb)
-            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fb + bb) * nn + fd + d));
-        atomicAdd(K + (fa + a) * nn + fc + c, (double)(s * t));
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fb + bb) * nn + fd + d);
+        atomicAdd(K + (fa + a) * nn + fc + c, to_f64(s * t));
     }
     for (int o = lane; o < NA * ND; o += 32) {          // K_ad = sum_bc I D_bc
         const int a = o / ND, d = o % ND;
         R t = R(0);
         for (int bb = 0; bb < NB; ++bb)
-            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fb + bb) * nn + fc + c));
-        atomicAdd(K + (fa + a) * nn + fd + d, (double)(s * t));
+            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fb + bb) * nn + fc + c);
+        atomicAdd(K + (fa + a) * nn + fd + d, to_f64(s * t));
     }
     for (int o = lane; o < NB * NC; o += 32) {          // K_bc = sum_ad I D_ad
         const int bb = o / NC, c = o % NC;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
-            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fa + a) * nn + fd + d));
-        atomicAdd(K + (fb + bb) * nn + fc + c, (double)(s * t));
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fa + a) * nn + fd + d);
+        atomicAdd(K + (fb + bb) * nn + fc + c, to_f64(s * t));
     }
     for (int o = lane; o < NB * ND; o += 32) {          // K_bd = sum_ac I D_ac
         const int bb = o / ND, d = o % ND;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
-            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * R(__ldg(D + (fa + a) * nn + fc + c));
-        atomicAdd(K + (fb + bb) * nn + fd + d, (double)(s * t));
+            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fa + a) * nn + fc + c);
+        atomicAdd(K + (fb + bb) * nn + fd + d, to_f64(s * t));
     }
 #undef MESS_I
 }

@@ -14,7 +14,8 @@ enum { MESS_MODE_FP64 = 0, MESS_MODE_MIXED = 1, MESS_MODE_FP32 = 2 };
 struct ClassLaunchArgs {
     int kind;                    // MESS_KIND_*
     int mode;                    // MESS_MODE_* (JK only)
-    int G;                       // JK: lanes per shell quartet (1 or 8)
+    int G;                       // JK: lanes per shell quartet (1, 4 or 8)
+    int team;                    // JK: 1 = one warp per shell quartet (level-scheduled program)
     BinLaunch bin;               // JK / STORE
     const int* pairs;            // SCHWARZ: pair ids of one diagonal class
     int npairs;

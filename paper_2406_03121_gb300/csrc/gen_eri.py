@@ -565,8 +565,7 @@ def emit_class_straight(cls):
     lines.append("    const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];")
     lines.append("    const int k0 = P.pp_off[kp], nk = P.pp_n[kp], k1 = k0 + nk;")
     lines.append("    // A - C in FP64, then P - Q = (P - A) - (Q - C) + (A - C): no absolute coordinates in R")
-    lines.append("    const R ACx = R(P.C[3 * bp] - P.C[3 * kp]), ACy = R(P.C[3 * bp + 1] - P.C[3 * kp + 1]);")
-    lines.append("    const R ACz = R(P.C[3 * bp + 2] - P.C[3 * kp + 2]);")
+    lines.append("    const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);")
     body = []
     body.append("            const R rz = R(1) / (pb.zeta + pk.zeta);")
     body.append("            const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;")
@@ -616,8 +615,8 @@ def emit_class_straight(cls):
     lines.append("#pragma unroll")
     lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = group_sum<G>(acc[k]);")
     lines.append("    }")
-    lines.append("    const R ABx = R(P.AB[3 * bp]), ABy = R(P.AB[3 * bp + 1]), ABz = R(P.AB[3 * bp + 2]);")
-    lines.append("    const R CDx = R(P.AB[3 * kp]), CDy = R(P.AB[3 * kp + 1]), CDz = R(P.AB[3 * kp + 2]);")
+    lines.append("    const R ABx = pair_ab(P, bp, 0), ABy = pair_ab(P, bp, 1), ABz = pair_ab(P, bp, 2);")
+    lines.append("    const R CDx = pair_ab(P, kp, 0), CDy = pair_ab(P, kp, 1), CDz = pair_ab(P, kp, 2);")
     lines.append("    (void)ABx; (void)ABy; (void)ABz; (void)CDx; (void)CDy; (void)CDz;")
     hb, hbf = hrr_bra(la, lb, v.fs, v.es, lines, "    ", "acc")
     hk, hkf = hrr_ket(lc, ld, v.fs, hb, la, lb, lines, "    ")
@@ -664,6 +663,21 @@ def emit_class(cls):
     L.append("};")
     L.append(f"__device__ const int fslot_{t}[{len(pr['fin'])}] = {{" + ", ".join(str(a) for a, _ in pr["fin"]) + "};")
     L.append(f"__device__ const double fscale_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(b) for _, b in pr["fin"]) + "};")
+    L.append("template <typename R, int BMODE, int G>")
+    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I)")
+    L.append("{")
+    L.append("    static_assert(G == 1, \"op-program classes run one thread per quartet\");")
+    L.append("    (void)g;")
+    L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
+             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kp, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, I);")
+    L.append("}")
+    return "\n".join(L) + "\n", info
+
+
+def emit_team(cls, info):
+    """Level-scheduled program arrays + kernel arguments of the warp-per-quartet kernel."""
+    t = tag(cls)
+    L = []
     tp = build_team_program(cls)
     info["team_nvi"], info["team_nh"] = max(tp["nv"], tp["nint"]), tp["nh"]
     L.append(f"// level-scheduled program for the warp-per-quartet J/K kernel: {len(tp['vlev']) - 1} VRR levels, "
@@ -674,9 +688,11 @@ def emit_class(cls):
         L.append(f"    {{{w0}u, {s1 | (s2 << 16)}u, {s3 | (s4 << 16)}u, {s5}u}},")
     L.append("};")
     L.append(f"__device__ const int tvlev_{t}[{len(tp['vlev'])}] = {{" + ", ".join(map(str, tp["vlev"])) + "};")
-    L.append(f"__device__ const uint2 thprog_{t}[{len(tp['hrr'])}] = {{")
+    L.append(f"__device__ const uint2 thprog_{t}[{max(1, len(tp['hrr']))}] = {{")
     for (tg, s1, s2, d, side) in tp["hrr"]:
         L.append(f"    {{{tg | (d << 16) | (side << 18)}u, {s1 | (s2 << 16)}u}},")
+    if not tp["hrr"]:
+        L.append("    {0u, 0u},")
     L.append("};")
     L.append(f"__device__ const int thlev_{t}[{len(tp['hlev'])}] = {{" + ", ".join(map(str, tp["hlev"])) + "};")
     L.append(f"__device__ const int tfslot_{t}[{len(tp['fin'])}] = {{" + ", ".join(str(a) for a, _ in tp["fin"]) + "};")
@@ -684,15 +700,13 @@ def emit_class(cls):
     L.append(f"#define MESS_TEAM_ARGS_{t} {tp['L']}, {max(tp['nv'], tp['nint'])}, {tp['nh']}, {tp['nacc']}, "
              f"{len(tp['vlev']) - 1}, {len(tp['hlev']) - 1}, {tp['nint']}, {tp['na']}, {tp['nb']}, {tp['nc']}, {tp['nd']}")
     L.append(f"#define MESS_TEAM_PROG_{t} tvprog_{t}, tvlev_{t}, thprog_{t}, thlev_{t}, tfslot_{t}, tfscale_{t}")
-    L.append("template <typename R, int BMODE, int G>")
-    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I)")
-    L.append("{")
-    L.append("    static_assert(G == 1, \"op-program classes run one thread per quartet\");")
-    L.append("    (void)g;")
-    L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
-             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kp, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, I);")
-    L.append("}")
-    return "\n".join(L) + "\n", info
+    return "\n".join(L) + "\n"
+
+
+def team_capable(info):
+    """classes that get a warp-per-quartet kernel (always used for the op-program classes; used for
+    the FP64 parts of the others)"""
+    return info["nvrr"] >= 40
 
 
 def emit_digest(cls, unroll=True):
@@ -717,10 +731,10 @@ def emit_digest(cls, unroll=True):
             L.append(PR)
             L.append(f"    for (int i = 0; i < {nr}; ++i)")
             L.append(PR)
-            L.append(f"        for (int j = 0; j < {ncol}; ++j) {nm}[i * {ncol} + j] = R(c.D[(size_t)({r0} + i) * c.n + {c0} + j]);")
+            L.append(f"        for (int j = 0; j < {ncol}; ++j) {nm}[i * {ncol} + j] = ldD<R>(c.D + (size_t)({r0} + i) * c.n + {c0} + j);")
             dref[nm] = lambda a, b, nm=nm, ncol=ncol: f"{nm}[{a} * {ncol} + {b}]"
         else:
-            dref[nm] = lambda a, b, r0=r0, c0=c0: f"R(__ldg(c.D + (size_t)({r0} + {a}) * c.n + {c0} + {b}))"
+            dref[nm] = lambda a, b, r0=r0, c0=c0: f"ldD<R>(c.D + (size_t)({r0} + {a}) * c.n + {c0} + {b})"
     I = f"I[((i * {nb} + j) * {nc} + k) * {nd} + l]"
     # J_ab
     L += [PR, f"    for (int i = 0; i < {na}; ++i)", PR, f"        for (int j = 0; j < {nb}; ++j) {{",
@@ -752,6 +766,8 @@ def main(outdir):
     infos = []
     for cls in QUARTET_CLASSES:
         body, info = emit_class(cls)
+        if team_capable(info) or info["mode"] == "program":
+            body += "\n" + emit_team(cls, info)
         dig = emit_digest(cls, unroll=(info['mode'] == 'straight'))
         path = os.path.join(outdir, f"eri_class_{info['tag']}.cuh")
         text = ("// Generated by gen_eri.py: do not edit.\n#pragma once\n#include \"eri_common.cuh\"\n\n"
@@ -769,7 +785,7 @@ def main(outdir):
         diag = (la, lb) == (lc, ld)
         u = ["// Generated by gen_eri.py: do not edit.", f'#include "eri_class_{t}.cuh"', '#include "eri_launch.h"', "",
              f"MESS_DEFINE_CLASS_KERNELS({t}, {na}, {nb}, {nc}, {nd})"]
-        team = info["mode"] == "program"
+        team = team_capable(info) or info["mode"] == "program"
         if team:
             u.append(f"MESS_DEFINE_TEAM_KERNEL({t})")
         if diag:
@@ -793,6 +809,7 @@ def main(outdir):
               f"        k_store_{t}<<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.out, a.n);",
               "    } else {",
               ] + ([
+              "      if (a.team) {",
               "        static int cfg[3][64];   // dynamic shared memory opt-in done, per kernel mode and device",
               "        const long long nbt = (a.bin.total + MESS_TEAM_WARPS - 1) / MESS_TEAM_WARPS;",
               "        if (nbt > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
@@ -803,19 +820,21 @@ def main(outdir):
               f"            return mess_team_launch<float, 1>(k_jk_team_{t}<float, 1>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[1]);",
               "        else",
               f"            return mess_team_launch<float, 2>(k_jk_team_{t}<float, 2>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[2]);",
-              ] if info["mode"] == "program" else []) + ([
-              "        if (a.G == 8) {",
-              "            const long long nb8 = (a.bin.total * 8 + T - 1) / T;",
-              "            if (nb8 > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
-              "            const dim3 g8((unsigned)nb8);",
+              "      }",
+              ] if (team_capable(info) or info["mode"] == "program") else []) + ([
+              ] + sum([[
+              f"        if (a.G == {GG}) {{",
+              f"            const long long nbg = (a.bin.total * {GG} + T - 1) / T;",
+              "            if (nbg > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
+              "            const dim3 gg((unsigned)nbg);",
               "            if (a.mode == MESS_MODE_FP64)",
-              f"                k_jk_{t}<double, 0, 8><<<g8, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
+              f"                k_jk_{t}<double, 0, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
               "            else if (a.mode == MESS_MODE_MIXED)",
-              f"                k_jk_{t}<float, 1, 8><<<g8, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              f"                k_jk_{t}<float, 1, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
               "            else",
-              f"                k_jk_{t}<float, 2, 8><<<g8, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              f"                k_jk_{t}<float, 2, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
               "            return cudaGetLastError();",
-              "        }"] if info["mode"] == "straight" else []) + [
+              "        }"] for GG in (4, 8)], []) if info["mode"] == "straight" else []) + [
               "        if (a.mode == MESS_MODE_FP64)",
               f"            k_jk_{t}<double, 0, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
               "        else if (a.mode == MESS_MODE_MIXED)",

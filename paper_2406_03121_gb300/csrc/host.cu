@@ -111,6 +111,9 @@ int pclass_of(int la, int lb)   // la >= lb
     return tab[la][lb];
 }
 
+// primitive-count group of a pair (lists are split so a launch's lanes run similar primitive loops)
+int prim_group(int npp) { return npp <= 3 ? 0 : (npp <= 12 ? 1 : 2); }
+
 int qclass_of(int p1, int p2)   // p1 >= p2
 {
     return p1 * (p1 + 1) / 2 + p2;
@@ -149,10 +152,15 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
     std::vector<long long> offs;
     for (int p1 = 0; p1 < MESS_NUM_PCLASS; ++p1) {
         for (int p2 = 0; p2 <= p1; ++p2) {
-            const std::vector<int>& bl = b->class_list[p1];
-            const std::vector<int>& kl = b->class_list[p2];
+        for (int g1 = 0; g1 < MESS_NGROUP; ++g1) {
+        for (int g2 = 0; g2 < MESS_NGROUP; ++g2) {
+            // unordered pairs of pairs of one class: list g1 x list g2 for g1 > g2, triangle for g1 == g2
+            if (p1 == p2 && g2 > g1) continue;
+            const int L1 = p1 * MESS_NGROUP + g1, L2 = p2 * MESS_NGROUP + g2;
+            const std::vector<int>& bl = b->class_list[L1];
+            const std::vector<int>& kl = b->class_list[L2];
             if (bl.empty() || kl.empty()) continue;
-            const bool same = p1 == p2;
+            const bool same = p1 == p2 && g1 == g2;
             const int nk = (int)kl.size();
             std::vector<double> qk(nk);
             std::vector<long long> fpre(nk + 1, 0), ppre(nk + 1, 0);
@@ -171,15 +179,15 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
                 bp.qclass = qclass_of(p1, p2);
                 bp.fp64 = fp64;
                 bp.bra_off = (int)bra.size();
-                bp.ket_list = p2;
+                bp.ket_list = L2;
                 bp.offs_off = offs.size();
                 bp.total = 0;
                 bp.fn_quartets = 0;
                 bp.prim_quartets = 0;
                 for (int m = 0; m < b->nmol; ++m) {
                     if (!b->active[m]) continue;
-                    const int bs0 = b->class_seg[p1][m], bs1 = b->class_seg[p1][m + 1];
-                    const int ks0 = b->class_seg[p2][m], ks1 = b->class_seg[p2][m + 1];
+                    const int bs0 = b->class_seg[L1][m], bs1 = b->class_seg[L1][m + 1];
+                    const int ks0 = b->class_seg[L2][m], ks1 = b->class_seg[L2][m + 1];
                     if (bs1 == bs0 || ks1 == ks0) continue;
                     // kets j in [ks0, ks1) (Q descending) with qi * qk[j] >= t: a prefix of the segment
                     auto count_ge = [&](double qi, double t) -> int {
@@ -219,10 +227,19 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
                 // heavily contracted quartets: split the primitive loop over 8 lanes
                 const bool straight = MESS_QCLASS[bp.qclass].nacc <= 96 && MESS_QCLASS[bp.qclass].nvrr <= 280;
                 const double avg = bp.total > 0 ? (double)bp.prim_quartets / (double)bp.total : 0.0;
-                bp.G = (straight && avg >= 24.0) ? 8 : 1;
+                // lanes per quartet: 8 for long primitive loops; 4 for medium loops of parts too small to
+                // fill the GPU one thread per quartet (measured: slower on parts of millions of quartets)
+                bp.G = !straight ? 1 : (avg >= 24.0 ? 8 : ((avg >= 6.0 && bp.total < (1LL << 18)) ? 4 : 1));
+                // warp per quartet: always for the op-program classes; for small FP64 parts of the classes
+                // with at least 40 VRR entries (too few quartets to fill the GPU one thread each:
+                // measured better below about 2e6 quartets x VRR entries, worse above)
+                const double work = (double)bp.total * MESS_QCLASS[bp.qclass].nvrr;
+                bp.team = (!straight || (fp64 && MESS_QCLASS[bp.qclass].nvrr >= 40 && bp.G == 1 && work < 2e6)) ? 1 : 0;
                 if (bp.nbra > 0) B.parts.push_back(bp);
                 else offs.resize(bp.offs_off);
             }
+        }
+        }
         }
     }
     if (B.bra.upload(bra) != cudaSuccess || B.kbeg.upload(kbeg) != cudaSuccess || B.offs.upload(offs) != cudaSuccess) {
@@ -361,6 +378,7 @@ static mess_status build_pairs(mess_basis* b)
     std::vector<PrimPairRec<double>> pp64;
     std::vector<PrimPairRec<float>> pp32;
     std::vector<double> AB, Ccen;
+    std::vector<float> ABf, Cf;
     std::vector<int> fa, fb, same;
     const double kpref = sqrt(2.0) * pow(M_PI, 1.25);
     for (int m = 0; m < b->nmol; ++m) {
@@ -382,8 +400,11 @@ static mess_status build_pairs(mess_basis* b)
                     ab[x] = sa.R[x] - sb.R[x];
                     ab2 += ab[x] * ab[x];
                     AB.push_back(ab[x]);
+                    ABf.push_back((float)ab[x]);
                     Ccen.push_back(sa.R[x]);
                 }
+                for (int x = 0; x < 3; ++x) Cf.push_back((float)sa.R[x]);
+                for (int x = 0; x < 3; ++x) Cf.push_back((float)(sa.R[x] - (double)(float)sa.R[x]));
                 for (int i = 0; i < sa.K; ++i)
                     for (int j = 0; j < sb.K; ++j) {
                         const double al = sa.alpha[i], be = sb.alpha[j], z = al + be;
@@ -414,6 +435,8 @@ static mess_status build_pairs(mess_basis* b)
     MESS_CUDA_TRY(b->d_pp_n.upload(b->pp_n));
     MESS_CUDA_TRY(b->d_AB.upload(AB));
     MESS_CUDA_TRY(b->d_Ccen.upload(Ccen));
+    MESS_CUDA_TRY(b->d_ABf.upload(ABf));
+    MESS_CUDA_TRY(b->d_Cf.upload(Cf));
     MESS_CUDA_TRY(b->d_fa.upload(fa));
     MESS_CUDA_TRY(b->d_fb.upload(fb));
     MESS_CUDA_TRY(b->d_same.upload(same));
@@ -437,6 +460,8 @@ static mess_status build_pairs(mess_basis* b)
     b->P64.fb = b->P32.fb = b->d_fb.p;
     b->P64.same = b->P32.same = b->d_same.p;
     b->P64.C = b->P32.C = b->d_Ccen.p;
+    b->P64.Cf = b->P32.Cf = b->d_Cf.p;
+    b->P64.ABf = b->P32.ABf = b->d_ABf.p;
     b->P64.mol = b->P32.mol = b->d_pair_mol.p;
     b->P64.mbase = b->P32.mbase = b->d_mol_base.p;
     b->P64.mn = b->P32.mn = b->d_mol_n.p;
@@ -490,20 +515,24 @@ static mess_status build_schwarz(mess_basis* b)
     MESS_CUDA_TRY(cudaMemcpy(b->Q.data(), b->d_Q.p, sizeof(double) * b->npair, cudaMemcpyDeviceToHost));
     for (int p = 0; p < b->npair; ++p)
         if (!std::isfinite(b->Q[p])) { mess_set_error("non-finite Schwarz factor for pair %d", p); return MESS_ENUMERIC; }
-    // class lists: per molecule, pairs sorted by Q descending
+    // lists per (class, primitive-count group): per molecule, pairs sorted by Q descending
     for (int c = 0; c < MESS_NUM_PCLASS; ++c) {
-        std::vector<std::vector<int>> per(b->nmol);
-        for (int p : lists[c]) per[b->pair_mol[p]].push_back(p);
-        std::vector<int> l;
-        std::vector<int> seg(1, 0);
-        for (int m = 0; m < b->nmol; ++m) {
-            std::stable_sort(per[m].begin(), per[m].end(), [&](int x, int y) { return b->Q[x] > b->Q[y]; });
-            l.insert(l.end(), per[m].begin(), per[m].end());
-            seg.push_back((int)l.size());
+        for (int g = 0; g < MESS_NGROUP; ++g) {
+            std::vector<std::vector<int>> per(b->nmol);
+            for (int p : lists[c])
+                if (prim_group(b->pp_n[p]) == g) per[b->pair_mol[p]].push_back(p);
+            std::vector<int> l;
+            std::vector<int> seg(1, 0);
+            for (int m = 0; m < b->nmol; ++m) {
+                std::stable_sort(per[m].begin(), per[m].end(), [&](int x, int y) { return b->Q[x] > b->Q[y]; });
+                l.insert(l.end(), per[m].begin(), per[m].end());
+                seg.push_back((int)l.size());
+            }
+            const int L = c * MESS_NGROUP + g;
+            b->class_list[L] = l;
+            b->class_seg[L] = seg;
+            MESS_CUDA_TRY(b->d_class_list[L].upload(l));
         }
-        b->class_list[c] = l;
-        b->class_seg[c] = seg;
-        MESS_CUDA_TRY(b->d_class_list[c].upload(l));
     }
     return MESS_OK;
 }
@@ -511,7 +540,7 @@ static mess_status build_schwarz(mess_basis* b)
 void mess_free_basis(mess_basis* b)
 {
     b->d_pp64.free(); b->d_pp32.free(); b->d_pp_off.free(); b->d_pp_n.free(); b->d_fa.free();
-    b->d_fb.free(); b->d_same.free(); b->d_AB.free(); b->d_Ccen.free(); b->d_Q.free(); b->d_boys64.free();
+    b->d_fb.free(); b->d_same.free(); b->d_AB.free(); b->d_Ccen.free(); b->d_ABf.free(); b->d_Cf.free(); b->d_Q.free(); b->d_boys64.free();
     b->d_boys32.free(); b->d_Z.free(); b->d_xyz.free(); b->d_shell_l.free(); b->d_shell_K.free();
     b->d_shell_f0.free(); b->d_shell_poff.free(); b->d_shell_R.free(); b->d_shell_alpha.free();
     b->d_shell_coef.free(); b->d_fscale.free(); b->d_pair_a.free(); b->d_pair_b.free();
@@ -734,6 +763,7 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
         a.kind = MESS_KIND_JK;
         a.mode = p.fp64 ? MESS_MODE_FP64 : (o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);
         a.G = p.G;
+        a.team = p.team;
         a.bin = bin_launch(b, p);
         a.P64_ptr = &b->P64;
         a.P32_ptr = &b->P32;

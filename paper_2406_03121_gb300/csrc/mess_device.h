@@ -14,6 +14,7 @@
 
 #define MESS_LMAX 2               // s, p, Cartesian d
 #define MESS_NUM_PCLASS 6         // pair classes (la,lb): ss ps pp ds dp dd
+#define MESS_NGROUP 3             // primitive-pair count groups: <= 3, 4..12, >= 13
 #define MESS_TEAM_WARPS 4         // warps (one shell quartet each) per block of the large-class kernels
 
 // One primitive pair: zeta, Px, Py, Pz, PAx, PAy, PAz, K, 1/(2 zeta) (+ padding to 16 bytes).

@@ -59,6 +59,7 @@ struct BinPart {
     int qclass;
     int fp64;              // 1: evaluated in FP64
     int G;                 // lanes per shell quartet (primitive loop split across G lanes)
+    int team;              // 1: one warp per shell quartet
     int bra_off, nbra;     // into the concatenated bra / kbeg / offs arrays
     int ket_list;          // pair class of the ket list
     long long total;       // shell quartets
@@ -97,14 +98,17 @@ struct mess_basis {
     int npair = 0;
     std::vector<int> pair_a, pair_b, pair_class, pp_off, pp_n, pair_mol;
     std::vector<double> Q;          // Schwarz factor per pair
-    std::vector<int> class_list[MESS_NUM_PCLASS];   // pair ids, per molecule sorted by Q descending
-    std::vector<int> class_seg[MESS_NUM_PCLASS];    // nmol + 1 segment offsets into class_list
-    DevBuf<int> d_class_list[MESS_NUM_PCLASS];
+    // pair lists per (pair class c, primitive-count group g) at index c * MESS_NGROUP + g: pair ids,
+    // per molecule sorted by Q descending, with nmol + 1 segment offsets
+    std::vector<int> class_list[MESS_NUM_PCLASS * MESS_NGROUP];
+    std::vector<int> class_seg[MESS_NUM_PCLASS * MESS_NGROUP];
+    DevBuf<int> d_class_list[MESS_NUM_PCLASS * MESS_NGROUP];
 
     DevBuf<PrimPairRec<double>> d_pp64;
     DevBuf<PrimPairRec<float>> d_pp32;
     DevBuf<int> d_pp_off, d_pp_n, d_fa, d_fb, d_same;
     DevBuf<double> d_AB, d_Q, d_Ccen;
+    DevBuf<float> d_ABf, d_Cf;
     DevBuf<double> d_boys64;
     DevBuf<float> d_boys32;
     DevBuf<int> d_Z;
