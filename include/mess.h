@@ -62,6 +62,9 @@ typedef struct {
                            0 selects MESS_DEFAULT_FP64_TAU, < 0 runs every quartet in FP32 */
     int boys_fp64;      /* MESS_MIXED / MESS_FP32: 1 evaluates the Boys function of the FP32 quartets
                            in FP64 for T < 36 (Taylor grid + downward recursion), 0 in FP32 */
+    int split_df32;     /* MESS_MIXED: 1 evaluates the quartets above fp64_tau in double-float
+                           arithmetic (pairs of FP32 values, about 48 bits, on the FP32 units: on this
+                           GPU several times faster than FP64) instead of FP64; 0 in FP64 */
     void* cuda_stream;  /* cudaStream_t for the device-pointer calls (NULL: default stream) */
 } mess_jk_opts;
 
@@ -89,6 +92,7 @@ typedef struct {
     double schwarz_tau;   /* screening threshold for the J/K builds */
     double fp64_tau;      /* MESS_MIXED split, see mess_jk_opts */
     int boys_fp64;        /* see mess_jk_opts */
+    int split_df32;       /* see mess_jk_opts */
     const char* mlp_weights; /* MESS_GUESS_MLP: weight file of mess_mlp_save (unused otherwise) */
     void* cuda_stream;
 } mess_scf_opts;

@@ -39,7 +39,7 @@ MLP_DIN, MLP_WIDTH, MLP_DOUT = 112, 256, 25
 
 class mess_jk_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("schwarz_tau", ctypes.c_double), ("fp64_tau", ctypes.c_double),
-                ("boys_fp64", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("boys_fp64", ctypes.c_int), ("split_df32", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
 
 
 class mess_jk_info(ctypes.Structure):
@@ -65,7 +65,7 @@ class mess_scf_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("guess", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("conv_E", ctypes.c_double), ("conv_comm", ctypes.c_double), ("diis_n", ctypes.c_int),
                 ("schwarz_tau", ctypes.c_double), ("fp64_tau", ctypes.c_double), ("boys_fp64", ctypes.c_int),
-                ("mlp_weights", ctypes.c_char_p), ("cuda_stream", ctypes.c_void_p)]
+                ("split_df32", ctypes.c_int), ("mlp_weights", ctypes.c_char_p), ("cuda_stream", ctypes.c_void_p)]
 
 
 class mess_scf_result(ctypes.Structure):
@@ -166,9 +166,10 @@ def _stream_handle(stream):
     return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
 
 
-def jk_opts(prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False) -> mess_jk_opts:
+def jk_opts(prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False, split_df32=False) -> mess_jk_opts:
     p = PRECISION[prec] if isinstance(prec, str) else int(prec)
-    return mess_jk_opts(p, float(schwarz_tau), float(fp64_tau), int(bool(boys_fp64)), _stream_handle(stream))
+    return mess_jk_opts(p, float(schwarz_tau), float(fp64_tau), int(bool(boys_fp64)), int(bool(split_df32)),
+                        _stream_handle(stream))
 
 
 class Basis:
@@ -248,36 +249,40 @@ class Basis:
         _check(mess_eri_tensor(self._h, _dptr(out)), "mess_eri_tensor")
         return out
 
-    def jk(self, D, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, boys_fp64=False):
+    def jk(self, D, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, boys_fp64=False, split_df32=False):
         """J, K of a host density (numpy); returns (J, K, info dict)."""
         D = np.ascontiguousarray(D, dtype=np.float64)
         J, K = np.zeros_like(D), np.zeros_like(D)
         info = mess_jk_info()
-        o = jk_opts(prec, schwarz_tau, fp64_tau, None, boys_fp64)
+        o = jk_opts(prec, schwarz_tau, fp64_tau, None, boys_fp64, split_df32)
         _check(mess_jk_build(self._h, _dptr(D), _dptr(J), _dptr(K), ctypes.byref(o), ctypes.byref(info)),
                "mess_jk_build")
         return J, K, info.as_dict()
 
-    def jk_device(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False):
+    def jk_device(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False,
+                  split_df32=False):
         """J, K of a device density (torch float64 CUDA tensors, caller-owned); enqueued on stream."""
         info = mess_jk_info()
-        o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64)
+        o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64, split_df32)
         _check(mess_jk_build_device(self._h, _tptr(D), _tptr(J), _tptr(K), ctypes.byref(o), ctypes.byref(info)),
                "mess_jk_build_device")
         return info.as_dict()
 
-    def jk_profile(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False):
+    def jk_profile(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False,
+                   split_df32=False):
         """Per-launch timings (CUDA events) and algorithmic flops of one device J/K build."""
         parts = (mess_jk_part * 1024)()
         n = ctypes.c_int()
-        o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64)
+        o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64, split_df32)
         _check(mess_jk_profile(self._h, _tptr(D), _tptr(J), _tptr(K), ctypes.byref(o), parts, 1024, ctypes.byref(n)),
                "mess_jk_profile")
         return [parts[i].as_dict() for i in range(n.value)]
 
     def scf(self, prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8, diis_n=8,
-            schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, want_density=True):
-        o = scf_opts(prec, guess, max_iter, conv_E, conv_comm, diis_n, schwarz_tau, fp64_tau, mlp_weights, stream)
+            schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, want_density=True, boys_fp64=False,
+            split_df32=False):
+        o = scf_opts(prec, guess, max_iter, conv_E, conv_comm, diis_n, schwarz_tau, fp64_tau, mlp_weights, stream,
+                     boys_fp64, split_df32)
         res = mess_scf_result()
         D = np.zeros((self.nbf, self.nbf)) if want_density else None
         st = mess_scf(self._h, ctypes.byref(o), ctypes.byref(res), _dptr(D) if D is not None else None)
@@ -297,20 +302,24 @@ def fma_peak(stream=None):
 
 
 def scf_opts(prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8, diis_n=8,
-             schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, boys_fp64=False) -> mess_scf_opts:
+             schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, boys_fp64=False,
+             split_df32=False) -> mess_scf_opts:
     p = PRECISION[prec] if isinstance(prec, str) else int(prec)
     w = os.fsencode(mlp_weights) if mlp_weights else None
     return mess_scf_opts(p, int(guess), int(max_iter), float(conv_E), float(conv_comm), int(diis_n),
-                         float(schwarz_tau), float(fp64_tau), int(bool(boys_fp64)), w, _stream_handle(stream))
+                         float(schwarz_tau), float(fp64_tau), int(bool(boys_fp64)), int(bool(split_df32)), w,
+                         _stream_handle(stream))
 
 
 def scf_batch(bases, prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8,
-              diis_n=8, schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None):
+              diis_n=8, schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, boys_fp64=False,
+              split_df32=False):
     """Batched SCF over many bases; returns a list of result dicts and the call's status."""
     n = len(bases)
     arr = (_P * n)(*[b.handle for b in bases])
     res = (mess_scf_result * n)()
-    o = scf_opts(prec, guess, max_iter, conv_E, conv_comm, diis_n, schwarz_tau, fp64_tau, mlp_weights, stream)
+    o = scf_opts(prec, guess, max_iter, conv_E, conv_comm, diis_n, schwarz_tau, fp64_tau, mlp_weights, stream,
+                 boys_fp64, split_df32)
     st = mess_scf_batch(n, arr, ctypes.byref(o), res)
     if st not in (MESS_OK, MESS_ENOCONV):
         _check(st, "mess_scf_batch")

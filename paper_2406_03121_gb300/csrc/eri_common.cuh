@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df32.cuh"
 #include "mess_device.h"
 
 // ------------------------------------------------------------------------------------------
@@ -18,34 +19,68 @@ template <typename R> struct PrimPair { R zeta, Px, Py, Pz, PAx, PAy, PAz, K, oo
 template <typename R> struct PairTable;
 
 // Conversions between FP64 and FP32 done on the integer ALU: on this GPU the FP64 pipe (which also
-// executes F2F conversions) runs at 1/64 of the FP32 rate, so FP32 kernels avoid it entirely.
-// Values outside the normal FP32 range (|x| < 2^-126 becomes 0; infinities / NaN) take the
-// hardware conversion.
+// executes F2F / I2F conversions) runs at 1/64 of the FP32 rate, so FP32 kernels avoid it entirely,
+// including in rarely taken branches (the compiler predicates them, and a predicated-off FP64-pipe
+// instruction still issues).  d2f: round to nearest with ties away from zero, results below 2^-126
+// flush to signed zero, overflow and infinities give signed infinity, NaN stays NaN.  f2d: exact; FP32 subnormals flush to zero.
 __device__ __forceinline__ float d2f_alu(double d)
 {
-    unsigned long long b = (unsigned long long)__double_as_longlong(d) + (1ull << 28);   // round to nearest
+    const unsigned long long o = (unsigned long long)__double_as_longlong(d);
+    const unsigned long long b = o + (1ull << 28);
+    const unsigned ohi = (unsigned)(o >> 32);
+    const unsigned sign = ohi & 0x80000000u;
     const unsigned hi = (unsigned)(b >> 32);
     const int fe = (int)((hi >> 20) & 0x7ffu) - 896;
-    if (fe <= 0) return __uint_as_float(hi & 0x80000000u);
-    if (fe >= 255) return (float)d;
-    return __uint_as_float((hi & 0x80000000u) | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
+    unsigned bits = sign | ((unsigned)fe << 23) | mant;
+    bits = fe <= 0 ? sign : bits;
+    bits = fe >= 255 ? (sign | 0x7f800000u) : bits;
+    bits = ((ohi >> 20) & 0x7ffu) == 0x7ffu ? (sign | 0x7f800000u | ((o << 12) ? 0x400000u : 0u)) : bits;
+    return __uint_as_float(bits);
 }
 
 __device__ __forceinline__ double f2d_alu(float f)
 {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-    if (e == 0xffu) return (double)f;
     const unsigned m = u & 0x7fffffu;
-    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+    const unsigned sign = u & 0x80000000u;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+    hi = e == 0u ? sign : hi;
+    hi = e == 0xffu ? (sign | 0x7ff00000u | (m >> 3)) : hi;
+    const unsigned lo = (e == 0u) ? 0u : (m << 29);
+    return __hiloint2double((int)hi, (int)lo);
 }
 
-template <typename R> __device__ __forceinline__ R ldD(const double* p);
-template <> __device__ __forceinline__ double ldD<double>(const double* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float ldD<float>(const double* p) { return d2f_alu(__ldg(p)); }
+// small non-negative integer to float without I2F: 2^23 + k as bits, minus 2^23 (0 <= k < 2^22)
+__device__ __forceinline__ float int_to_f32_alu(int k) { return __int_as_float(0x4B000000 | k) - 8388608.0f; }
+
+template <typename R> __device__ __forceinline__ R small_int(int k);
+template <> __device__ __forceinline__ double small_int<double>(int k) { return (double)k; }
+template <> __device__ __forceinline__ float small_int<float>(int k) { return int_to_f32_alu(k); }
+template <> __device__ __forceinline__ df32 small_int<df32>(int k) { return df32(int_to_f32_alu(k), 0.f); }
+
+// a generated per-integral scale (double with float hi / lo copies) in R
+template <typename R> __device__ __forceinline__ R gen_scale(const double* d, const float* hi, const float* lo, int k);
+template <> __device__ __forceinline__ double gen_scale<double>(const double* d, const float*, const float*, int k) { return __ldg(d + k); }
+template <> __device__ __forceinline__ float gen_scale<float>(const double*, const float* hi, const float*, int k) { return __ldg(hi + k); }
+template <> __device__ __forceinline__ df32 gen_scale<df32>(const double*, const float* hi, const float* lo, int k)
+{ return df32(__ldg(hi + k), __ldg(lo + k)); }
+
+// double -> double-float: hi rounded to nearest, lo the rounded remainder (one FP64 subtraction)
+__device__ __forceinline__ df32::df32(double v)
+{
+    hi = d2f_alu(v);
+    lo = d2f_alu(v - f2d_alu(hi));
+}
+
+// density elements: the FP32 and double-float kernels read copies of D converted once per build
+__device__ __forceinline__ double ldD(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldD(const float* p) { return __ldg(p); }
+__device__ __forceinline__ df32 ldD(const float2* p) { const float2 v = __ldg(p); return df32(v.x, v.y); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 __device__ __forceinline__ double to_f64(float v) { return f2d_alu(v); }
+__device__ __forceinline__ double to_f64(df32 v) { return f2d_alu(v.hi) + f2d_alu(v.lo); }
 
 template <typename R> struct PairTable {
     const PrimPairRec<R>* __restrict__ pp;   // [npp]
@@ -63,6 +98,7 @@ template <typename R> struct PairTable {
     const int* __restrict__ mn;              // [nmol] basis functions of the molecule (row stride)
     const double* __restrict__ boys64;       // Boys grid, FP64
     const float* __restrict__ boys32;        // Boys grid, FP32
+    const float2* __restrict__ boysdf;       // Boys grid, double-float (hi, lo)
 
     __device__ __forceinline__ PrimPair<R> load(int i) const
     {
@@ -85,7 +121,14 @@ __device__ __forceinline__ float pair_ac(const PairTable<float>& P, int bp, int 
 {
     return (__ldg(P.Cf + 6 * bp + x) - __ldg(P.Cf + 6 * kp + x)) + (__ldg(P.Cf + 6 * bp + 3 + x) - __ldg(P.Cf + 6 * kp + 3 + x));
 }
+__device__ __forceinline__ df32 pair_ac(const PairTable<df32>& P, int bp, int kp, int x)
+{
+    const df32 h = df_two_sum(__ldg(P.Cf + 6 * bp + x), -__ldg(P.Cf + 6 * kp + x));
+    const df32 l = df_two_sum(__ldg(P.Cf + 6 * bp + 3 + x), -__ldg(P.Cf + 6 * kp + 3 + x));
+    return h + l;
+}
 __device__ __forceinline__ double pair_ab(const PairTable<double>& P, int p, int x) { return P.AB[3 * p + x]; }
+__device__ __forceinline__ df32 pair_ab(const PairTable<df32>& P, int p, int x) { return df32(P.AB[3 * p + x]); }
 __device__ __forceinline__ float pair_ab(const PairTable<float>& P, int p, int x) { return __ldg(P.ABf + 3 * p + x); }
 
 // ------------------------------------------------------------------------------------------
@@ -174,30 +217,81 @@ template <int L> __device__ __forceinline__ void boys_large_f32(float T, float* 
     }
 }
 
-template <typename R, int L, int BMODE>
-__device__ __forceinline__ void boys_eval(R T, R* F, const double* t64, const float* t32);
+// double-float Boys: the same grid expansion and recursions in df32 arithmetic (grid in hi/lo
+// pairs); above the grid F_0 = sqrt(pi)/2 T^-1/2 and the upward recursion, whose exp(-T) term
+// (below 3e-16 there) is taken in FP32.
+__device__ __forceinline__ df32 df_inv_int(int j)   // 1/j as double-float
+{
+    const float h = 1.0f / (float)j;
+    return df32(h, fmaf(-h, (float)j, 1.0f) / (float)j);
+}
 
-template <> __device__ __forceinline__ void boys_eval<double, 0, 0>(double T, double* F, const double* t64, const float*)
-{ if (T < MESS_BOYS_TMAX64) boys_small_f64<0>(T, F, t64); else boys_large_f64<0>(T, F); }
+template <int L> __device__ __forceinline__ void boys_small_df(df32 T, df32* F, const float2* __restrict__ tab)
+{
+    const float r = fmaf(T.hi, (float)MESS_BOYS_INV_DT, 12582912.0f);
+    const int k = __float_as_int(r) - 0x4B400000;
+    const df32 dt(0.1f, -1.490116119384765625e-9f);   // 0.1 = hi + lo to 48 bits
+    const df32 x = df32(k) * dt - T;                  // T_k - T
+    const float2* row = tab + (size_t)k * MESS_BOYS_NCOL;
+    const float2 t7 = __ldg(row + L + 7);
+    df32 s(t7.x, t7.y);
+#pragma unroll
+    for (int j = 7; j >= 1; --j) {
+        const float2 tj = __ldg(row + L + j - 1);
+        s = df32(tj.x, tj.y) + s * x * df_inv_int(j);
+    }
+    F[L] = s;
+    if (L == 0) return;
+    df32 ex = df32(1.0f, 0.f);
+#pragma unroll
+    for (int j = 9; j >= 1; --j) ex = df32(1.0f, 0.f) + x * df_inv_int(j) * ex;
+    const float2 te = __ldg(row + MESS_BOYS_NF);
+    const df32 e = df32(te.x, te.y) * ex;
+    const df32 t2 = T + T;
+#pragma unroll
+    for (int m = L; m >= 1; --m) F[m - 1] = (t2 * F[m] + e) * df_inv_int(2 * m - 1);
+}
+
+template <int L> __device__ __forceinline__ void boys_large_df(df32 T, df32* F)
+{
+    const df32 rt = df32(1.0f, 0.f) / df_sqrt(T);
+    F[0] = df32(0.8862269520759583f, -2.6623199644859596e-08f) * rt;   // sqrt(pi)/2 = 0.88622692545275801 as hi + lo
+    if (L > 0) {
+        const df32 e(__expf(-T.hi), 0.f);
+        const df32 h = df32(0.5f, 0.f) / T;
+#pragma unroll
+        for (int m = 0; m < L; ++m) F[m + 1] = (df32(2 * m + 1) * F[m] - e) * h;
+    }
+}
+
+template <typename R> struct PairTable;
+template <typename R, int L, int BMODE>
+__device__ __forceinline__ void boys_eval(R T, R* F, const PairTable<R>& P);
+
+template <> __device__ __forceinline__ void boys_eval<double, 0, 0>(double T, double* F, const PairTable<double>& P)
+{ if (T < MESS_BOYS_TMAX64) boys_small_f64<0>(T, F, P.boys64); else boys_large_f64<0>(T, F); }
 
 #define MESS_BOYS_SPECIALISE(LL)                                                                  \
     template <> __device__ __forceinline__ void boys_eval<double, LL, 0>(double T, double* F,     \
-                                                                        const double* t64, const float*) \
-    { if (T < MESS_BOYS_TMAX64) boys_small_f64<LL>(T, F, t64); else boys_large_f64<LL>(T, F); }   \
+                                                                        const PairTable<double>& P) \
+    { if (T < MESS_BOYS_TMAX64) boys_small_f64<LL>(T, F, P.boys64); else boys_large_f64<LL>(T, F); } \
     template <> __device__ __forceinline__ void boys_eval<float, LL, 1>(float T, float* F,        \
-                                                                       const double* t64, const float*) \
+                                                                       const PairTable<float>& P) \
     {                                                                                             \
         if (T < (float)MESS_BOYS_TMAX64) {                                                        \
             double Fd[LL + 1];                                                                    \
-            boys_small_f64<LL>((double)T, Fd, t64);                                               \
+            boys_small_f64<LL>((double)T, Fd, P.boys64);                                          \
             _Pragma("unroll") for (int m = 0; m <= LL; ++m) F[m] = (float)Fd[m];                  \
         } else {                                                                                  \
             boys_large_f32<LL>(T, F);                                                             \
         }                                                                                         \
     }                                                                                             \
     template <> __device__ __forceinline__ void boys_eval<float, LL, 2>(float T, float* F,        \
-                                                                       const double*, const float* t32) \
-    { if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<LL>(T, F, t32); else boys_large_f32<LL>(T, F); }
+                                                                       const PairTable<float>& P) \
+    { if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<LL>(T, F, P.boys32); else boys_large_f32<LL>(T, F); } \
+    template <> __device__ __forceinline__ void boys_eval<df32, LL, 3>(df32 T, df32* F,           \
+                                                                      const PairTable<df32>& P)   \
+    { if (T < MESS_BOYS_TMAX64) boys_small_df<LL>(T, F, P.boysdf); else boys_large_df<LL>(T, F); }
 
 MESS_BOYS_SPECIALISE(1)
 MESS_BOYS_SPECIALISE(2)
@@ -208,16 +302,19 @@ MESS_BOYS_SPECIALISE(6)
 MESS_BOYS_SPECIALISE(7)
 MESS_BOYS_SPECIALISE(8)
 
-template <> __device__ __forceinline__ void boys_eval<float, 0, 1>(float T, float* F, const double* t64, const float*)
+template <> __device__ __forceinline__ void boys_eval<float, 0, 1>(float T, float* F, const PairTable<float>& P)
 {
-    if (T < (float)MESS_BOYS_TMAX64) { double Fd[1]; boys_small_f64<0>((double)T, Fd, t64); F[0] = (float)Fd[0]; }
+    if (T < (float)MESS_BOYS_TMAX64) { double Fd[1]; boys_small_f64<0>((double)T, Fd, P.boys64); F[0] = (float)Fd[0]; }
     else boys_large_f32<0>(T, F);
 }
-template <> __device__ __forceinline__ void boys_eval<float, 0, 2>(float T, float* F, const double*, const float* t32)
-{ if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<0>(T, F, t32); else boys_large_f32<0>(T, F); }
+template <> __device__ __forceinline__ void boys_eval<float, 0, 2>(float T, float* F, const PairTable<float>& P)
+{ if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<0>(T, F, P.boys32); else boys_large_f32<0>(T, F); }
+template <> __device__ __forceinline__ void boys_eval<df32, 0, 3>(df32 T, df32* F, const PairTable<df32>& P)
+{ if (T < MESS_BOYS_TMAX64) boys_small_df<0>(T, F, P.boysdf); else boys_large_df<0>(T, F); }
 
 __device__ __forceinline__ double prefactor_sqrt(double rz) { return sqrt(rz); }
 __device__ __forceinline__ float prefactor_sqrt(float rz) { return sqrtf(rz); }
+__device__ __forceinline__ df32 prefactor_sqrt(df32 rz) { return df_sqrt(rz); }
 
 // ------------------------------------------------------------------------------------------
 // J/K accumulation.  For a unique shell quartet (ab|cd) (pair ab >= pair cd, a >= b, c >= d by
@@ -228,8 +325,8 @@ __device__ __forceinline__ float prefactor_sqrt(float rz) { return sqrtf(rz); }
 // and afterwards J = 2 (Jacc + Jacc^T), K = Kacc + Kacc^T.  This visits each of the 8 index
 // permutations of every function quartet exactly once for a symmetric D.
 // ------------------------------------------------------------------------------------------
-struct DigestCtx {
-    const double* __restrict__ D;
+template <typename R> struct DigestCtx {
+    const typename DElem<R>::T* __restrict__ D;
     double* __restrict__ J;
     double* __restrict__ K;
     int n;
@@ -237,18 +334,22 @@ struct DigestCtx {
     bool warp_reduce_ab;   // all 32 lanes share the bra pair: reduce J_ab across the warp first
 };
 
+__device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df32 shfl_xor(df32 v, int o) { return df_shfl_xor(v, o); }
+
 // sum over aligned groups of G consecutive lanes (G a power of two); every lane of the warp takes part
 template <int G, typename R> __device__ __forceinline__ R group_sum(R v)
 {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = G / 2; o > 0; o >>= 1) v += shfl_xor(v, o);
     return v;
 }
 
 template <typename R> __device__ __forceinline__ R warp_sum(R v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
     return v;
 }
 
@@ -290,7 +391,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
 #define MESS_DEFINE_CLASS_KERNELS(TAG, NA, NB, NC, ND)                                             \
     template <typename R, int BMODE, int G>                                                         \
     __global__ void __launch_bounds__(MESS_THREADS)                                                 \
-    k_jk_##TAG(const BinLaunch b, const PairTable<R> P, const double* __restrict__ D,               \
+    k_jk_##TAG(const BinLaunch b, const PairTable<R> P, const typename DElem<R>::T* __restrict__ D,            \
                double* __restrict__ J, double* __restrict__ K, int n)                               \
     {                                                                                               \
         const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;                     \
@@ -303,7 +404,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);                                     \
         R I[(NA) * (NB) * (NC) * (ND)];                                                             \
         eri_##TAG<R, BMODE, G>(P, bp, kp, g, I);                                                    \
-        DigestCtx c;                                                                                \
+        DigestCtx<R> c;                                                                              \
         {                                                                                           \
             const int m_ = __ldg(P.mol + bp);                                                       \
             const long long o_ = __ldg(P.mbase + m_);                                               \
@@ -396,6 +497,7 @@ template <typename R, int BMODE, int L, int NV, int NH, int NACC, int NVOPS, int
 __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int kp,
                                             const uint4* __restrict__ vprog, const uint2* __restrict__ hprog,
                                             const int* __restrict__ fslot, const double* __restrict__ fscale,
+                                            const float* __restrict__ fscale_hi, const float* __restrict__ fscale_lo,
                                             R* I)
 {
     R V[NV];
@@ -419,7 +521,7 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
             const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);
             const R pref = pb.K * pk.K * prefactor_sqrt(rz);
             R F[L + 1];
-            boys_eval<R, L, BMODE>(T, F, P.boys64, P.boys32);
+            boys_eval<R, L, BMODE>(T, F, P);
 #pragma unroll
             for (int m = 0; m <= L; ++m) F[m] *= pref;
 #pragma unroll 1
@@ -439,11 +541,11 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
                     R v;
                     if (kind == 1) {
                         v = pick3(d, pb.PAx, pb.PAy, pb.PAz) * V[s1] + pick3(d, WPx, WPy, WPz) * V[s2];
-                        if (m1) v += R(m1) * pb.oo2z * (V[w.z & 0xffff] - roz * V[w.z >> 16]);
+                        if (m1) v += small_int<R>(m1) * pb.oo2z * (V[w.z & 0xffff] - roz * V[w.z >> 16]);
                     } else {
                         v = pick3(d, pk.PAx, pk.PAy, pk.PAz) * V[s1] + pick3(d, WQx, WQy, WQz) * V[s2];
-                        if (m1) v += R(m1) * pk.oo2z * (V[w.z & 0xffff] - roe * V[w.z >> 16]);
-                        if (m2) v += R(m2) * oo2ze * V[w.w];
+                        if (m1) v += small_int<R>(m1) * pk.oo2z * (V[w.z & 0xffff] - roe * V[w.z >> 16]);
+                        if (m2) v += small_int<R>(m2) * oo2ze * V[w.w];
                     }
                     V[t] = v;
                 }
@@ -460,7 +562,7 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
         H[t] = H[w.y & 0xffff] + X * H[w.y >> 16];
     }
 #pragma unroll 1
-    for (int k = 0; k < NINT; ++k) I[k] = R(__ldg(fscale + k)) * H[__ldg(fslot + k)];
+    for (int k = 0; k < NINT; ++k) I[k] = gen_scale<R>(fscale, fscale_hi, fscale_lo, k) * H[__ldg(fslot + k)];
 }
 
 
@@ -472,11 +574,12 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
 
 template <typename R, int BMODE, int L, int NVI, int NH, int NACC, int NVL, int NHL, int NINT,
           int NA, int NB, int NC, int ND>
-__device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable<R>& P, const double* __restrict__ D,
+__device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable<R>& P, const typename DElem<R>::T* __restrict__ D,
                                              double* __restrict__ J, double* __restrict__ K, int n,
                                              const uint4* __restrict__ vprog, const int* __restrict__ vlev,
                                              const uint2* __restrict__ hprog, const int* __restrict__ hlev,
                                              const int* __restrict__ fslot, const double* __restrict__ fscale,
+                                             const float* __restrict__ fscale_hi, const float* __restrict__ fscale_lo,
                                              R* __restrict__ sm)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -506,7 +609,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
             const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);
             const R pref = pb.K * pk.K * prefactor_sqrt(rz);
             R F[L + 1];
-            boys_eval<R, L, BMODE>(T, F, P.boys64, P.boys32);
+            boys_eval<R, L, BMODE>(T, F, P);
 #pragma unroll
             for (int m = 0; m <= L; ++m) F[m] *= pref;
 #pragma unroll 1
@@ -527,12 +630,12 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
                         H[s1] += V[t];
                     } else if (kind == 1) {
                         R v = pick3(d, pb.PAx, pb.PAy, pb.PAz) * V[s1] + pick3(d, WPx, WPy, WPz) * V[s2];
-                        if (m1) v += R(m1) * pb.oo2z * (V[w.z & 0xffff] - roz * V[w.z >> 16]);
+                        if (m1) v += small_int<R>(m1) * pb.oo2z * (V[w.z & 0xffff] - roz * V[w.z >> 16]);
                         V[t] = v;
                     } else {
                         R v = pick3(d, pk.PAx, pk.PAy, pk.PAz) * V[s1] + pick3(d, WQx, WQy, WQz) * V[s2];
-                        if (m1) v += R(m1) * pk.oo2z * (V[w.z & 0xffff] - roe * V[w.z >> 16]);
-                        if (m2) v += R(m2) * oo2ze * V[w.w];
+                        if (m1) v += small_int<R>(m1) * pk.oo2z * (V[w.z & 0xffff] - roe * V[w.z >> 16]);
+                        if (m2) v += small_int<R>(m2) * oo2ze * V[w.w];
                         V[t] = v;
                     }
                 }
@@ -554,7 +657,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
         }
         __syncwarp();
     }
-    for (int k = lane; k < NINT; k += 32) V[k] = R(__ldg(fscale + k)) * H[__ldg(fslot + k)];
+    for (int k = lane; k < NINT; k += 32) V[k] = gen_scale<R>(fscale, fscale_hi, fscale_lo, k) * H[__ldg(fslot + k)];
     __syncwarp();
     const R* I = V;
     R s = R(1);
@@ -574,42 +677,42 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
         const int a = o / NB, bb = o % NB;
         R t = R(0);
         for (int c = 0; c < NC; ++c)
-            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fc + c) * nn + fd + d);
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD(D + (fc + c) * nn + fd + d);
         atomicAdd(J + (fa + a) * nn + fb + bb, to_f64(s * t));
     }
     for (int o = lane; o < NC * ND; o += 32) {          // J_cd = sum_ab I D_ab
         const int c = o / ND, d = o % ND;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
-            for (int bb = 0; bb < NB; ++bb) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fa + a) * nn + fb + bb);
+            for (int bb = 0; bb < NB; ++bb) t += MESS_I(a, bb, c, d) * ldD(D + (fa + a) * nn + fb + bb);
         atomicAdd(J + (fc + c) * nn + fd + d, to_f64(s * t));
     }
     for (int o = lane; o < NA * NC; o += 32) {          // K_ac = sum_bd I D_bd
         const int a = o / NC, c = o % NC;
         R t = R(0);
         for (int bb = 0; bb < NB; ++bb)
-            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fb + bb) * nn + fd + d);
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD(D + (fb + bb) * nn + fd + d);
         atomicAdd(K + (fa + a) * nn + fc + c, to_f64(s * t));
     }
     for (int o = lane; o < NA * ND; o += 32) {          // K_ad = sum_bc I D_bc
         const int a = o / ND, d = o % ND;
         R t = R(0);
         for (int bb = 0; bb < NB; ++bb)
-            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fb + bb) * nn + fc + c);
+            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * ldD(D + (fb + bb) * nn + fc + c);
         atomicAdd(K + (fa + a) * nn + fd + d, to_f64(s * t));
     }
     for (int o = lane; o < NB * NC; o += 32) {          // K_bc = sum_ad I D_ad
         const int bb = o / NC, c = o % NC;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
-            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fa + a) * nn + fd + d);
+            for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD(D + (fa + a) * nn + fd + d);
         atomicAdd(K + (fb + bb) * nn + fc + c, to_f64(s * t));
     }
     for (int o = lane; o < NB * ND; o += 32) {          // K_bd = sum_ac I D_ac
         const int bb = o / ND, d = o % ND;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
-            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * ldD<R>(D + (fa + a) * nn + fc + c);
+            for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * ldD(D + (fa + a) * nn + fc + c);
         atomicAdd(K + (fb + bb) * nn + fd + d, to_f64(s * t));
     }
 #undef MESS_I
@@ -622,7 +725,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     }                                                                                               \
     template <typename R, int BMODE>                                                                \
     __global__ void __launch_bounds__(32 * MESS_TEAM_WARPS)                                         \
-    k_jk_team_##TAG(const BinLaunch b, const PairTable<R> P, const double* __restrict__ D,          \
+    k_jk_team_##TAG(const BinLaunch b, const PairTable<R> P, const typename DElem<R>::T* __restrict__ D,          \
                     double* __restrict__ J, double* __restrict__ K, int n)                          \
     {                                                                                               \
         extern __shared__ __align__(16) unsigned char mess_team_smem[];                             \

@@ -2,14 +2,16 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "df32.cuh"
 #include "eri_classes.h"
 #include "mess_device.h"
 
 template <typename R> struct PairTable;
 
 enum { MESS_KIND_JK = 0, MESS_KIND_STORE = 1, MESS_KIND_SCHWARZ = 2 };
-// kernel modes: FP64; FP32 recursion with FP64 Boys at small T; FP32 recursion with FP32 Boys
-enum { MESS_MODE_FP64 = 0, MESS_MODE_MIXED = 1, MESS_MODE_FP32 = 2 };
+// kernel modes: FP64; FP32 recursion with FP64 Boys at small T; FP32 recursion with FP32 Boys;
+// double-float (FP32 pairs) recursion and Boys
+enum { MESS_MODE_FP64 = 0, MESS_MODE_MIXED = 1, MESS_MODE_FP32 = 2, MESS_MODE_DF32 = 3 };
 
 struct ClassLaunchArgs {
     int kind;                    // MESS_KIND_*
@@ -21,13 +23,21 @@ struct ClassLaunchArgs {
     int npairs;
     const PairTable<double>* P64_ptr;
     const PairTable<float>* P32_ptr;
+    const PairTable<df32>* Pdf_ptr;
     const double* D;             // device, n x n
+    const float* D32;            // D rounded to FP32 (FP32 kernels)
+    const float2* Ddf;           // D as double-float hi, lo (double-float kernels)
     double* J;                   // device, n x n accumulators
     double* K;
     double* out;                 // STORE: n^4 tensor; SCHWARZ: Q per pair
     int n;
     cudaStream_t stream;
 };
+
+template <typename R> inline const typename DElem<R>::T* dmat(const ClassLaunchArgs& a);
+template <> inline const double* dmat<double>(const ClassLaunchArgs& a) { return a.D; }
+template <> inline const float* dmat<float>(const ClassLaunchArgs& a) { return a.D32; }
+template <> inline const float2* dmat<df32>(const ClassLaunchArgs& a) { return a.Ddf; }
 
 typedef cudaError_t (*mess_class_launcher)(const ClassLaunchArgs&);
 extern const mess_class_launcher MESS_CLASS_LAUNCHERS[MESS_NUM_QCLASS];
@@ -47,6 +57,6 @@ cudaError_t mess_team_launch(Kern kern, dim3 grid, size_t smem, const ClassLaunc
         if (e != cudaSuccess) return e;
         configured[dev] = 1;
     }
-    kern<<<grid, 32 * MESS_TEAM_WARPS, smem, a.stream>>>(a.bin, P, a.D, a.J, a.K, a.n);
+    kern<<<grid, 32 * MESS_TEAM_WARPS, smem, a.stream>>>(a.bin, P, dmat<R>(a), a.J, a.K, a.n);
     return cudaGetLastError();
 }

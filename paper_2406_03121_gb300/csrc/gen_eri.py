@@ -23,6 +23,8 @@ import math
 import os
 import sys
 
+import numpy as np
+
 PAIR_CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
 QUARTET_CLASSES = [(PAIR_CLASSES[i], PAIR_CLASSES[j])
                    for i in range(len(PAIR_CLASSES)) for j in range(i + 1)]
@@ -581,7 +583,7 @@ def emit_class_straight(cls):
     body.append("            const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);")
     body.append("            const R pref = pb.K * pk.K * prefactor_sqrt(rz);")
     body.append(f"            R F[{L + 1}];")
-    body.append(f"            boys_eval<R, {L}, BMODE>(T, F, P.boys64, P.boys32);")
+    body.append(f"            boys_eval<R, {L}, BMODE>(T, F, P);")
     body.append("#pragma unroll")
     body.append(f"            for (int m = 0; m <= {L}; ++m) F[m] *= pref;")
     vflops = v.emit(body, "            ")
@@ -663,13 +665,18 @@ def emit_class(cls):
     L.append("};")
     L.append(f"__device__ const int fslot_{t}[{len(pr['fin'])}] = {{" + ", ".join(str(a) for a, _ in pr["fin"]) + "};")
     L.append(f"__device__ const double fscale_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(b) for _, b in pr["fin"]) + "};")
+    his = [float(np.float32(b)) for _, b in pr["fin"]]
+    los = [float(np.float32(b - h)) for (_, b), h in zip(pr["fin"], his)]
+    L.append(f"__device__ const float fscaleh_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(h) + "f" for h in his) + "};")
+    L.append(f"__device__ const float fscalel_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(l) + "f" for l in los) + "};")
     L.append("template <typename R, int BMODE, int G>")
     L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I)")
     L.append("{")
     L.append("    static_assert(G == 1, \"op-program classes run one thread per quartet\");")
     L.append("    (void)g;")
     L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
-             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kp, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, I);")
+             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kp, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, "
+             f"fscaleh_{t}, fscalel_{t}, I);")
     L.append("}")
     return "\n".join(L) + "\n", info
 
@@ -697,9 +704,14 @@ def emit_team(cls, info):
     L.append(f"__device__ const int thlev_{t}[{len(tp['hlev'])}] = {{" + ", ".join(map(str, tp["hlev"])) + "};")
     L.append(f"__device__ const int tfslot_{t}[{len(tp['fin'])}] = {{" + ", ".join(str(a) for a, _ in tp["fin"]) + "};")
     L.append(f"__device__ const double tfscale_{t}[{len(tp['fin'])}] = {{" + ", ".join(repr(b) for _, b in tp["fin"]) + "};")
+    his = [float(np.float32(b)) for _, b in tp["fin"]]
+    los = [float(np.float32(b - h)) for (_, b), h in zip(tp["fin"], his)]
+    L.append(f"__device__ const float tfscaleh_{t}[{len(tp['fin'])}] = {{" + ", ".join(repr(h) + "f" for h in his) + "};")
+    L.append(f"__device__ const float tfscalel_{t}[{len(tp['fin'])}] = {{" + ", ".join(repr(l) + "f" for l in los) + "};")
     L.append(f"#define MESS_TEAM_ARGS_{t} {tp['L']}, {max(tp['nv'], tp['nint'])}, {tp['nh']}, {tp['nacc']}, "
              f"{len(tp['vlev']) - 1}, {len(tp['hlev']) - 1}, {tp['nint']}, {tp['na']}, {tp['nb']}, {tp['nc']}, {tp['nd']}")
-    L.append(f"#define MESS_TEAM_PROG_{t} tvprog_{t}, tvlev_{t}, thprog_{t}, thlev_{t}, tfslot_{t}, tfscale_{t}")
+    L.append(f"#define MESS_TEAM_PROG_{t} tvprog_{t}, tvlev_{t}, thprog_{t}, thlev_{t}, tfslot_{t}, tfscale_{t}, "
+             f"tfscaleh_{t}, tfscalel_{t}")
     return "\n".join(L) + "\n"
 
 
@@ -719,7 +731,7 @@ def emit_digest(cls, unroll=True):
     PR = "#pragma unroll" if unroll else "#pragma unroll 1"
     L = []
     L.append(f"template <typename R>")
-    L.append(f"__device__ __forceinline__ void digest_{t}(const R* I, const DigestCtx& c, R s)")
+    L.append(f"__device__ __forceinline__ void digest_{t}(const R* I, const DigestCtx<R>& c, R s)")
     L.append("{")
     blocks = (("Dab", ("c.fa", na), ("c.fb", nb)), ("Dcd", ("c.fc", nc), ("c.fd", nd)),
               ("Dac", ("c.fa", na), ("c.fc", nc)), ("Dad", ("c.fa", na), ("c.fd", nd)),
@@ -731,10 +743,10 @@ def emit_digest(cls, unroll=True):
             L.append(PR)
             L.append(f"    for (int i = 0; i < {nr}; ++i)")
             L.append(PR)
-            L.append(f"        for (int j = 0; j < {ncol}; ++j) {nm}[i * {ncol} + j] = ldD<R>(c.D + (size_t)({r0} + i) * c.n + {c0} + j);")
+            L.append(f"        for (int j = 0; j < {ncol}; ++j) {nm}[i * {ncol} + j] = ldD(c.D + (size_t)({r0} + i) * c.n + {c0} + j);")
             dref[nm] = lambda a, b, nm=nm, ncol=ncol: f"{nm}[{a} * {ncol} + {b}]"
         else:
-            dref[nm] = lambda a, b, r0=r0, c0=c0: f"ldD<R>(c.D + (size_t)({r0} + {a}) * c.n + {c0} + {b})"
+            dref[nm] = lambda a, b, r0=r0, c0=c0: f"ldD(c.D + (size_t)({r0} + {a}) * c.n + {c0} + {b})"
     I = f"I[((i * {nb} + j) * {nc} + k) * {nd} + l]"
     # J_ab
     L += [PR, f"    for (int i = 0; i < {na}; ++i)", PR, f"        for (int j = 0; j < {nb}; ++j) {{",
@@ -810,7 +822,7 @@ def main(outdir):
               "    } else {",
               ] + ([
               "      if (a.team) {",
-              "        static int cfg[3][64];   // dynamic shared memory opt-in done, per kernel mode and device",
+              "        static int cfg[4][64];   // dynamic shared memory opt-in done, per kernel mode and device",
               "        const long long nbt = (a.bin.total + MESS_TEAM_WARPS - 1) / MESS_TEAM_WARPS;",
               "        if (nbt > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
               "        const dim3 gt((unsigned)nbt);",
@@ -818,6 +830,8 @@ def main(outdir):
               f"            return mess_team_launch<double, 0>(k_jk_team_{t}<double, 0>, gt, team_smem_{t}<double>(), a, *a.P64_ptr, cfg[0]);",
               "        else if (a.mode == MESS_MODE_MIXED)",
               f"            return mess_team_launch<float, 1>(k_jk_team_{t}<float, 1>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[1]);",
+              "        else if (a.mode == MESS_MODE_DF32)",
+              f"            return mess_team_launch<df32, 3>(k_jk_team_{t}<df32, 3>, gt, team_smem_{t}<df32>(), a, *a.Pdf_ptr, cfg[3]);",
               "        else",
               f"            return mess_team_launch<float, 2>(k_jk_team_{t}<float, 2>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[2]);",
               "      }",
@@ -828,19 +842,23 @@ def main(outdir):
               "            if (nbg > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
               "            const dim3 gg((unsigned)nbg);",
               "            if (a.mode == MESS_MODE_FP64)",
-              f"                k_jk_{t}<double, 0, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
+              f"                k_jk_{t}<double, 0, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P64_ptr, dmat<double>(a), a.J, a.K, a.n);",
               "            else if (a.mode == MESS_MODE_MIXED)",
-              f"                k_jk_{t}<float, 1, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              f"                k_jk_{t}<float, 1, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P32_ptr, dmat<float>(a), a.J, a.K, a.n);",
+              "            else if (a.mode == MESS_MODE_DF32)",
+              f"                k_jk_{t}<df32, 3, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.Pdf_ptr, dmat<df32>(a), a.J, a.K, a.n);",
               "            else",
-              f"                k_jk_{t}<float, 2, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              f"                k_jk_{t}<float, 2, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P32_ptr, dmat<float>(a), a.J, a.K, a.n);",
               "            return cudaGetLastError();",
               "        }"] for GG in (4, 8)], []) if info["mode"] == "straight" else []) + [
               "        if (a.mode == MESS_MODE_FP64)",
-              f"            k_jk_{t}<double, 0, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, a.D, a.J, a.K, a.n);",
+              f"            k_jk_{t}<double, 0, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, dmat<double>(a), a.J, a.K, a.n);",
               "        else if (a.mode == MESS_MODE_MIXED)",
-              f"            k_jk_{t}<float, 1, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              f"            k_jk_{t}<float, 1, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, dmat<float>(a), a.J, a.K, a.n);",
+              "        else if (a.mode == MESS_MODE_DF32)",
+              f"            k_jk_{t}<df32, 3, 1><<<g, T, 0, a.stream>>>(a.bin, *a.Pdf_ptr, dmat<df32>(a), a.J, a.K, a.n);",
               "        else",
-              f"            k_jk_{t}<float, 2, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, a.D, a.J, a.K, a.n);",
+              f"            k_jk_{t}<float, 2, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P32_ptr, dmat<float>(a), a.J, a.K, a.n);",
               "    }",
               "    return cudaGetLastError();",
               "}"]

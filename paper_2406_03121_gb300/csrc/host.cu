@@ -247,10 +247,25 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
         B.tau = -1.0;
         return MESS_ECUDA;
     }
+    // the reduced-precision density copies (and their reuse event) come with the bins, so that a
+    // build with ready bins allocates nothing
+    if (split != 0) {
+        cudaError_t e = cudaSuccess;
+        if (b->d_D32.n != (size_t)b->packed) e = b->d_D32.alloc((size_t)b->packed);
+        if (e == cudaSuccess && split == 2 && b->d_Ddf.n != (size_t)b->packed) e = b->d_Ddf.alloc((size_t)b->packed);
+        if (e == cudaSuccess && !b->dconv_free) e = cudaEventCreateWithFlags(&b->dconv_free, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            mess_set_error("density copies: %s", cudaGetErrorString(e));
+            B.tau = -1.0;
+            return MESS_ECUDA;
+        }
+    }
     B.tau = tau;
     B.tau64 = tau64;
     B.split = split;
     B.active_version = b->active_version;
+    B.generation += 1;
+    mess_free_jk_graphs(b);
     return MESS_OK;
 }
 
@@ -263,6 +278,7 @@ struct StreamPool {
     bool init = false;
     cudaStream_t s[MESS_NSTREAMS];
     cudaEvent_t fork, join[MESS_NSTREAMS];
+    cudaStream_t capture;   // private stream on which J/K graphs are captured
     std::mutex mu;
 };
 static StreamPool g_pools[64];
@@ -281,6 +297,7 @@ static cudaError_t get_pool(StreamPool** out)
             if ((e = cudaEventCreateWithFlags(&P.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
         }
         if ((e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&P.capture, cudaStreamNonBlocking)) != cudaSuccess) return e;
         P.init = true;
     }
     *out = &P;
@@ -377,6 +394,7 @@ static mess_status build_pairs(mess_basis* b)
     }
     std::vector<PrimPairRec<double>> pp64;
     std::vector<PrimPairRec<float>> pp32;
+    std::vector<PrimPairRec<df32>> ppdf;
     std::vector<double> AB, Ccen;
     std::vector<float> ABf, Cf;
     std::vector<int> fa, fb, same;
@@ -419,8 +437,14 @@ static mess_status build_pairs(mess_basis* b)
                         r.v[8] = 0.5 / z;
                         pp64.push_back(r);
                         PrimPairRec<float> f{};
-                        for (int k = 0; k < 12; ++k) f.v[k] = (float)r.v[k];
+                        PrimPairRec<df32> g;
+                        for (int k = 0; k < 12; ++k) {
+                            f.v[k] = (float)r.v[k];
+                            g.v[k].hi = (float)r.v[k];
+                            g.v[k].lo = (float)(r.v[k] - (double)g.v[k].hi);
+                        }
                         pp32.push_back(f);
+                        ppdf.push_back(g);
                     }
                 b->pp_n.push_back(sa.K * sb.K);
                 fa.push_back(sa.fl);
@@ -431,6 +455,7 @@ static mess_status build_pairs(mess_basis* b)
     }
     MESS_CUDA_TRY(b->d_pp64.upload(pp64));
     MESS_CUDA_TRY(b->d_pp32.upload(pp32));
+    MESS_CUDA_TRY(b->d_ppdf.upload(ppdf));
     MESS_CUDA_TRY(b->d_pp_off.upload(b->pp_off));
     MESS_CUDA_TRY(b->d_pp_n.upload(b->pp_n));
     MESS_CUDA_TRY(b->d_AB.upload(AB));
@@ -445,6 +470,12 @@ static mess_status build_pairs(mess_basis* b)
     MESS_CUDA_TRY(b->d_boys64.upload(tab));
     std::vector<float> tab32(tab.begin(), tab.end());
     MESS_CUDA_TRY(b->d_boys32.upload(tab32));
+    std::vector<float2> tabdf(tab.size());
+    for (size_t i = 0; i < tab.size(); ++i) {
+        tabdf[i].x = (float)tab[i];
+        tabdf[i].y = (float)(tab[i] - (double)tabdf[i].x);
+    }
+    MESS_CUDA_TRY(b->d_boysdf.upload(tabdf));
     MESS_CUDA_TRY(b->d_pair_mol.upload(b->pair_mol));
     MESS_CUDA_TRY(b->d_mol_base.upload(b->mol_base));
     MESS_CUDA_TRY(b->d_mol_n.upload(b->mol_nbf));
@@ -467,6 +498,13 @@ static mess_status build_pairs(mess_basis* b)
     b->P64.mn = b->P32.mn = b->d_mol_n.p;
     b->P64.boys64 = b->P32.boys64 = b->d_boys64.p;
     b->P64.boys32 = b->P32.boys32 = b->d_boys32.p;
+    b->P64.boysdf = b->P32.boysdf = b->d_boysdf.p;
+    // the double-float table shares every per-pair array with the others
+    b->Pdf.pp = b->d_ppdf.p;
+    b->Pdf.pp_off = b->P64.pp_off; b->Pdf.pp_n = b->P64.pp_n; b->Pdf.AB = b->P64.AB; b->Pdf.fa = b->P64.fa;
+    b->Pdf.fb = b->P64.fb; b->Pdf.same = b->P64.same; b->Pdf.C = b->P64.C; b->Pdf.Cf = b->P64.Cf;
+    b->Pdf.ABf = b->P64.ABf; b->Pdf.mol = b->P64.mol; b->Pdf.mbase = b->P64.mbase; b->Pdf.mn = b->P64.mn;
+    b->Pdf.boys64 = b->d_boys64.p; b->Pdf.boys32 = b->d_boys32.p; b->Pdf.boysdf = b->d_boysdf.p;
     // shells for the one-electron kernels
     std::vector<int> sl, sK, sf0, spoff;
     std::vector<double> sR, sal, sco;
@@ -539,7 +577,7 @@ static mess_status build_schwarz(mess_basis* b)
 
 void mess_free_basis(mess_basis* b)
 {
-    b->d_pp64.free(); b->d_pp32.free(); b->d_pp_off.free(); b->d_pp_n.free(); b->d_fa.free();
+    b->d_pp64.free(); b->d_pp32.free(); b->d_ppdf.free(); b->d_boysdf.free(); b->d_pp_off.free(); b->d_pp_n.free(); b->d_fa.free();
     b->d_fb.free(); b->d_same.free(); b->d_AB.free(); b->d_Ccen.free(); b->d_ABf.free(); b->d_Cf.free(); b->d_Q.free(); b->d_boys64.free();
     b->d_boys32.free(); b->d_Z.free(); b->d_xyz.free(); b->d_shell_l.free(); b->d_shell_K.free();
     b->d_shell_f0.free(); b->d_shell_poff.free(); b->d_shell_R.free(); b->d_shell_alpha.free();
@@ -548,6 +586,10 @@ void mess_free_basis(mess_basis* b)
     b->d_f_local.free(); b->d_mol_base.free();
     for (auto& d : b->d_class_list) d.free();
     b->bins.bra.free(); b->bins.kbeg.free(); b->bins.offs.free();
+    mess_free_jk_graphs(b);
+    b->d_D32.free(); b->d_Ddf.free();
+    if (b->dconv_free) cudaEventDestroy(b->dconv_free);
+    b->dconv_free = nullptr;
 }
 
 extern "C" mess_status mess_basis_create(int natom, const int* Z, const double* xyz_bohr, const char* basis_file,
@@ -702,8 +744,119 @@ static void class_flops(int qc, double* per_prim, double* per_shell)
     *per_shell = (double)c.hrr_flops + 12.0 * c.nint;
 }
 
+// The launches of one J/K build, all on stream s or forked from it onto the pool's streams and
+// joined back: zero J and K, convert D for the reduced-precision parts, one launch per bin part
+// (most expensive first), symmetrise.  With parts != null every launch runs on s between timing
+// events.  Used directly and under stream capture (the cached CUDA graph of a repeated build).
+static mess_status jk_enqueue(mess_basis* b, const mess_jk_opts& o, const double* dD, double* dJ, double* dK,
+                              cudaStream_t s, bool need32, bool needdf, StreamPool* pool,
+                              std::vector<cudaEvent_t>* ev, mess_jk_info* info)
+{
+    const size_t bytes = (size_t)b->packed * sizeof(double);
+    MESS_CUDA_TRY(cudaMemsetAsync(dJ, 0, bytes, s));
+    MESS_CUDA_TRY(cudaMemsetAsync(dK, 0, bytes, s));
+    mess_jk_info inf{};
+    if (need32 || needdf) {
+        MESS_CUDA_TRY(mess_launch_convert_density(dD, need32 ? b->d_D32.p : nullptr, needdf ? b->d_Ddf.p : nullptr,
+                                                  b->packed, s));
+        inf.kernel_launches += 1;
+    }
+    // launch order: most expensive parts first (FP64, then by algorithmic work)
+    std::vector<size_t> order(b->bins.parts.size());
+    std::iota(order.begin(), order.end(), (size_t)0);
+    auto cost = [&](const BinPart& p) {
+        double fp, fs;
+        class_flops(p.qclass, &fp, &fs);
+        return (fp * (double)p.prim_quartets + fs * (double)p.total) * (p.fp64 ? 62.0 : 1.0);
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return cost(b->bins.parts[x]) > cost(b->bins.parts[y]); });
+    const bool concurrent = pool != nullptr;
+    if (concurrent) {
+        MESS_CUDA_TRY(cudaEventRecord(pool->fork, s));
+        for (int i = 0; i < MESS_NSTREAMS; ++i) MESS_CUDA_TRY(cudaStreamWaitEvent(pool->s[i], pool->fork, 0));
+    }
+    mess_status out = MESS_OK;
+    for (size_t r = 0; r < order.size(); ++r) {
+        const size_t k = order[r];
+        const BinPart& p = b->bins.parts[k];
+        ClassLaunchArgs a{};
+        a.kind = MESS_KIND_JK;
+        a.mode = p.fp64 ? ((o.prec == MESS_MIXED && o.split_df32) ? MESS_MODE_DF32 : MESS_MODE_FP64)
+                        : (o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);
+        a.G = p.G;
+        a.team = p.team;
+        a.bin = bin_launch(b, p);
+        a.P64_ptr = &b->P64;
+        a.P32_ptr = &b->P32;
+        a.Pdf_ptr = &b->Pdf;
+        a.D = dD;
+        a.D32 = b->d_D32.p;
+        a.Ddf = b->d_Ddf.p;
+        a.J = dJ;
+        a.K = dK;
+        a.n = b->nbf;
+        a.stream = concurrent ? pool->s[r % MESS_NSTREAMS] : s;
+        if (ev) cudaEventRecord((*ev)[2 * k], s);
+        cudaError_t e = MESS_CLASS_LAUNCHERS[p.qclass](a);
+        if (ev) cudaEventRecord((*ev)[2 * k + 1], s);
+        if (e != cudaSuccess) {
+            mess_set_error("J/K kernel launch (class %d): %s", p.qclass, cudaGetErrorString(e));
+            out = MESS_ECUDA;
+            break;
+        }
+        inf.shell_quartets += p.total;
+        inf.function_quartets += p.fn_quartets;
+        inf.primitive_quartets += p.prim_quartets;
+        if (p.fp64) inf.shell_quartets_fp64 += p.total;
+        inf.kernel_launches += 1;
+    }
+    if (concurrent) {
+        // join: s waits for every pool stream (also after a failed launch)
+        for (int i = 0; i < MESS_NSTREAMS; ++i) {
+            cudaEventRecord(pool->join[i], pool->s[i]);
+            cudaStreamWaitEvent(s, pool->join[i], 0);
+        }
+    }
+    if (out == MESS_OK) {
+        cudaError_t e = mess_launch_symmetrise_jk(b, dJ, dK, s);
+        if (e != cudaSuccess) { mess_set_error("symmetrise: %s", cudaGetErrorString(e)); out = MESS_ECUDA; }
+        inf.kernel_launches += 1;
+    }
+    *info = inf;
+    return out;
+}
+
+void mess_free_jk_graphs(mess_basis* b)
+{
+    for (JKGraph& g : b->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+}
+
+// Capture the launches of one build into a graph on a private stream (thread-local capture mode,
+// pool streams forked into the capture) and instantiate it.  Returns null if any step fails; the
+// build then launches directly.
+static cudaGraphExec_t jk_capture(mess_basis* b, const mess_jk_opts& o, const double* dD, double* dJ, double* dK,
+                                  bool need32, bool needdf, StreamPool* pool, mess_jk_info* info)
+{
+    cudaStream_t cs = pool->capture;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+    mess_status st = jk_enqueue(b, o, dD, dJ, dK, cs, need32, needdf, b->bins.parts.size() > 1 ? pool : nullptr,
+                                nullptr, info);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (st == MESS_OK && e == cudaSuccess && graph) {
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();   // a failed capture leaves nothing sticky; clear the last-error slot
+    return exec;
+}
+
 static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
-                          mess_jk_info* info, mess_jk_part* parts, int max_parts, int* nparts)
+                          mess_jk_info* info, mess_jk_part* parts, int max_parts, int* nparts, bool graphs = true)
 {
     if (!b || !dD || !dJ || !dK) { mess_set_error("null argument"); return MESS_EINVAL; }
     if (dD == dJ || dD == dK || dJ == dK) { mess_set_error("D, J and K must be distinct buffers"); return MESS_EINVAL; }
@@ -726,81 +879,28 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
         return MESS_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)o.cuda_stream;
-    const int n = b->nbf;
-    const size_t bytes = (size_t)b->packed * sizeof(double);
-    MESS_CUDA_TRY(cudaMemsetAsync(dJ, 0, bytes, s));
-    MESS_CUDA_TRY(cudaMemsetAsync(dK, 0, bytes, s));
-    std::vector<cudaEvent_t> ev;
-    if (parts) {
-        ev.resize(2 * b->bins.parts.size());
-        for (auto& e : ev) MESS_CUDA_TRY(cudaEventCreate(&e));
+    // FP32 / double-float copies of D for the reduced-precision parts, made once per build; the
+    // previous build on this basis must be done with them first
+    bool need32 = false, needdf = false;
+    for (const BinPart& p : b->bins.parts) {
+        if (!p.fp64) need32 = true;
+        else if (o.prec == MESS_MIXED && o.split_df32) needdf = true;
     }
-    // launch order: most expensive parts first (FP64, then by algorithmic work)
-    std::vector<size_t> order(b->bins.parts.size());
-    std::iota(order.begin(), order.end(), (size_t)0);
-    auto cost = [&](const BinPart& p) {
-        double fp, fs;
-        class_flops(p.qclass, &fp, &fs);
-        return (fp * (double)p.prim_quartets + fs * (double)p.total) * (p.fp64 ? 62.0 : 1.0);
-    };
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t x, size_t y) { return cost(b->bins.parts[x]) > cost(b->bins.parts[y]); });
-    StreamPool* pool = nullptr;
-    std::unique_lock<std::mutex> lk;
-    const bool concurrent = !parts && b->bins.parts.size() > 1;
-    if (concurrent) {
-        MESS_CUDA_TRY(get_pool(&pool));
-        lk = std::unique_lock<std::mutex>(pool->mu);
-        MESS_CUDA_TRY(cudaEventRecord(pool->fork, s));
-        for (int i = 0; i < MESS_NSTREAMS; ++i) MESS_CUDA_TRY(cudaStreamWaitEvent(pool->s[i], pool->fork, 0));
+    if ((need32 && !b->d_D32.p) || (needdf && !b->d_Ddf.p) || ((need32 || needdf) && !b->dconv_free)) {
+        mess_set_error("density copies missing");
+        return MESS_ECUDA;
     }
+    if (need32 || needdf) MESS_CUDA_TRY(cudaStreamWaitEvent(s, b->dconv_free, 0));
     mess_jk_info inf{};
     mess_status out = MESS_OK;
-    for (size_t r = 0; r < order.size(); ++r) {
-        const size_t k = order[r];
-        const BinPart& p = b->bins.parts[k];
-        ClassLaunchArgs a{};
-        a.kind = MESS_KIND_JK;
-        a.mode = p.fp64 ? MESS_MODE_FP64 : (o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);
-        a.G = p.G;
-        a.team = p.team;
-        a.bin = bin_launch(b, p);
-        a.P64_ptr = &b->P64;
-        a.P32_ptr = &b->P32;
-        a.D = dD;
-        a.J = dJ;
-        a.K = dK;
-        a.n = n;
-        a.stream = concurrent ? pool->s[r % MESS_NSTREAMS] : s;
-        if (parts) cudaEventRecord(ev[2 * k], s);
-        cudaError_t e = MESS_CLASS_LAUNCHERS[p.qclass](a);
-        if (parts) cudaEventRecord(ev[2 * k + 1], s);
-        if (e != cudaSuccess) {
-            mess_set_error("J/K kernel launch (class %d): %s", p.qclass, cudaGetErrorString(e));
-            out = MESS_ECUDA;
-            break;
+    if (parts) {
+        std::vector<cudaEvent_t> ev(2 * b->bins.parts.size());
+        for (auto& e : ev) MESS_CUDA_TRY(cudaEventCreate(&e));
+        out = jk_enqueue(b, o, dD, dJ, dK, s, need32, needdf, nullptr, &ev, &inf);
+        if (out == MESS_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { mess_set_error("profile sync: %s", cudaGetErrorString(e)); out = MESS_ECUDA; }
         }
-        inf.shell_quartets += p.total;
-        inf.function_quartets += p.fn_quartets;
-        inf.primitive_quartets += p.prim_quartets;
-        if (p.fp64) inf.shell_quartets_fp64 += p.total;
-        inf.kernel_launches += 1;
-    }
-    if (concurrent) {
-        // join: the caller's stream waits for every pool stream (also after a failed launch)
-        for (int i = 0; i < MESS_NSTREAMS; ++i) {
-            cudaEventRecord(pool->join[i], pool->s[i]);
-            cudaStreamWaitEvent(s, pool->join[i], 0);
-        }
-    }
-    if (out == MESS_OK) {
-        cudaError_t e = mess_launch_symmetrise_jk(b, dJ, dK, s);
-        if (e != cudaSuccess) { mess_set_error("symmetrise: %s", cudaGetErrorString(e)); out = MESS_ECUDA; }
-        inf.kernel_launches += 1;
-    }
-    if (parts && out == MESS_OK) {
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { mess_set_error("profile sync: %s", cudaGetErrorString(e)); out = MESS_ECUDA; }
         for (size_t k = 0; out == MESS_OK && k < b->bins.parts.size(); ++k) {
             const BinPart& p = b->bins.parts[k];
             const mess_qclass_info& c = MESS_QCLASS[p.qclass];
@@ -818,9 +918,46 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
             cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
             r.ms = ms;
         }
-        if (nparts) *nparts = (int)b->bins.parts.size();
+        if (out == MESS_OK && nparts) *nparts = (int)b->bins.parts.size();
+        for (auto& e : ev) cudaEventDestroy(e);
+    } else {
+        StreamPool* pool = nullptr;
+        MESS_CUDA_TRY(get_pool(&pool));
+        std::unique_lock<std::mutex> lk(pool->mu);
+        // A build repeated with the same buffers, options and bins (an SCF loop, a benchmark) runs
+        // as one CUDA graph launch instead of one launch per part: captured on the second such call,
+        // replayed from the third.  Not while the caller's stream is itself being captured.
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        MESS_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+        JKGraph* g = nullptr;
+        if (graphs && cap == cudaStreamCaptureStatusNone) {
+            for (JKGraph& x : b->graphs)
+                if (x.bins_gen == b->bins.generation && x.prec == o.prec && x.boys_fp64 == o.boys_fp64 &&
+                    x.split_df32 == o.split_df32 && x.D == dD && x.J == dJ && x.K == dK) g = &x;
+            if (!g) {
+                if (b->graphs.size() >= 4) {
+                    if (b->graphs.front().exec) cudaGraphExecDestroy(b->graphs.front().exec);
+                    b->graphs.erase(b->graphs.begin());
+                }
+                JKGraph x{};
+                x.bins_gen = b->bins.generation;
+                x.prec = o.prec; x.boys_fp64 = o.boys_fp64; x.split_df32 = o.split_df32;
+                x.D = dD; x.J = dJ; x.K = dK;
+                b->graphs.push_back(x);
+            } else if (!g->exec && !g->failed) {
+                g->exec = jk_capture(b, o, dD, dJ, dK, need32, needdf, pool, &g->info);
+                if (!g->exec) g->failed = 1;
+            }
+        }
+        if (g && g->exec) {
+            MESS_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+            inf = g->info;
+        } else {
+            out = jk_enqueue(b, o, dD, dJ, dK, s, need32, needdf, b->bins.parts.size() > 1 ? pool : nullptr, nullptr,
+                             &inf);
+        }
     }
-    for (auto& e : ev) cudaEventDestroy(e);
+    if (need32 || needdf) cudaEventRecord(b->dconv_free, s);
     if (info) *info = inf;
     return out;
 }
@@ -832,9 +969,9 @@ extern "C" mess_status mess_jk_build_device(const mess_basis* bc, const double* 
 }
 
 mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
-                           mess_jk_info* info)
+                           mess_jk_info* info, bool graphs)
 {
-    return jk_run(b, dD, dJ, dK, opts, info, nullptr, 0, nullptr);
+    return jk_run(b, dD, dJ, dK, opts, info, nullptr, 0, nullptr, graphs);
 }
 
 bool mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts)

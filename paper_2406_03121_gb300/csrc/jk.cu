@@ -1,5 +1,7 @@
 // Finishing step of the J/K build: J = 2 (Jacc + Jacc^T), K = Kacc + Kacc^T, in place, for every
 // molecule block of the packed matrices.
+#include <algorithm>
+
 #include "mess_internal.h"
 
 namespace {
@@ -26,7 +28,30 @@ __global__ void k_symmetrise_jk(double* __restrict__ J, double* __restrict__ K, 
     Km[ij] = ks; Km[ji] = ks;
 }
 
+// Copies of D read by the reduced-precision J/K kernels: FP32 (round to nearest) and double-float
+// (hi = D rounded to FP32, lo = the remainder rounded to FP32).  Either output may be null.
+__global__ void k_convert_density(const double* __restrict__ D, float* __restrict__ D32, float2* __restrict__ Ddf,
+                                  long long count)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = D[i];
+        const float hi = __double2float_rn(v);
+        if (D32) D32[i] = hi;
+        if (Ddf) Ddf[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
 }  // namespace
+
+cudaError_t mess_launch_convert_density(const double* D, float* D32, float2* Ddf, long long count, cudaStream_t s)
+{
+    if (count <= 0 || (!D32 && !Ddf)) return cudaSuccess;
+    const int T = 256;
+    const long long blocks = std::min<long long>((count + T - 1) / T, 4LL * 152);
+    k_convert_density<<<(unsigned)blocks, T, 0, s>>>(D, D32, Ddf, count);
+    return cudaGetLastError();
+}
 
 cudaError_t mess_launch_symmetrise_jk(const mess_basis* b, double* J, double* K, cudaStream_t s)
 {

@@ -74,7 +74,7 @@ extern "C" mess_status mess_jk_build_static(const mess_basis* bc, const double* 
     const size_t nn = (size_t)n * n;
     double *dD = w, *dJ = w + nn, *dK = w + 2 * nn;
     MESS_CUDA_TRY(cudaMemcpyAsync(dD, D, nn * sizeof(double), cudaMemcpyHostToDevice, s));
-    st = mess_jk_packed(b, dD, dJ, dK, &o, info);
+    st = mess_jk_packed(b, dD, dJ, dK, &o, info, /*graphs=*/false);
     if (st != MESS_OK) return st;
     MESS_CUDA_TRY(cudaMemcpyAsync(J, dJ, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
     MESS_CUDA_TRY(cudaMemcpyAsync(K, dK, nn * sizeof(double), cudaMemcpyDeviceToHost, s));

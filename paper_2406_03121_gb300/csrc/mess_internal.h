@@ -72,9 +72,23 @@ struct BinSet {
     double tau = -1.0, tau64 = -1.0;
     int split = -1;        // whether an FP64 / FP32 split was requested
     long long active_version = -1;
+    long long generation = 0;   // incremented on every rebuild (cached graphs refer to one generation)
     std::vector<BinPart> parts;
     DevBuf<int> bra, kbeg;
     DevBuf<long long> offs;
+};
+
+// An instantiated CUDA graph of one J/K build: the bins' generation, the options that select
+// kernels and the D / J / K buffers it was captured with.
+struct JKGraph {
+    long long bins_gen = -1;
+    int prec = 0, boys_fp64 = 0, split_df32 = 0;
+    const double* D = nullptr;
+    double* J = nullptr;
+    double* K = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int failed = 0;            // capture or instantiation failed once: launch directly
+    mess_jk_info info{};
 };
 
 // A basis of one molecule, or (internally) of a batch of molecules: shells, pairs and quartets
@@ -120,13 +134,25 @@ struct mess_basis {
 
     PairTable<double> P64;
     PairTable<float> P32;
+    PairTable<df32> Pdf;
+    DevBuf<PrimPairRec<df32>> d_ppdf;
+    DevBuf<float2> d_boysdf;
     BinSet bins;
+    // reduced-precision copies of the density of the J/K build in flight (allocated with the bins);
+    // a build waits on dconv_free (recorded when the previous build's kernels are done) before
+    // overwriting them
+    DevBuf<float> d_D32;
+    DevBuf<float2> d_Ddf;
+    cudaEvent_t dconv_free = nullptr;
+    std::vector<JKGraph> graphs;   // J/K graphs of repeated builds (at most 4, oldest dropped first)
 };
 
 // one-electron integrals on the device (one_e.cu)
 cudaError_t mess_launch_one_e(const mess_basis* b, double* dS, double* dT, double* dV, cudaStream_t s);
 // J/K helpers (jk.cu)
 cudaError_t mess_launch_symmetrise_jk(const mess_basis* b, double* J, double* K, cudaStream_t s);
+// FP32 and double-float copies of the packed density (either output may be null)
+cudaError_t mess_launch_convert_density(const double* D, float* D32, float2* Ddf, long long count, cudaStream_t s);
 // Boys tables (boys_table.cu): rows x MESS_BOYS_NCOL
 void mess_boys_table(std::vector<double>& tab);
 // bins (host.cu)
@@ -144,4 +170,5 @@ mess_status mess_mlp_guess_device(const mess_mlp* m, const mess_basis* b, double
 bool mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts);
 // J/K on packed device matrices of (possibly batched) bases (host.cu)
 mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
-                           mess_jk_info* info);
+                           mess_jk_info* info, bool graphs = true);
+void mess_free_jk_graphs(mess_basis* b);

@@ -635,6 +635,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
     jo.schwarz_tau = o.schwarz_tau;
     jo.fp64_tau = o.fp64_tau;
     jo.boys_fp64 = o.boys_fp64;
+    jo.split_df32 = o.split_df32;
     jo.cuda_stream = st.s;
     int nstored = 0, slot = 0, remaining = b->nmol;
     mess_status status = MESS_OK;

@@ -96,16 +96,17 @@ def water2_scf(oracle_mod):
     return mol, r.D, J, K
 
 
-@pytest.mark.parametrize("prec,fp64_tau,boys64,tol", [
-    ("mixed", 0.0, False, 1e-6),     # default split (Q_ab Q_cd >= 3e-2 in FP64): the reduced-precision bar
-    ("mixed", 1e-3, True, 1e-6),
-    ("mixed", -1.0, False, 2e-5),    # no FP64 quartets at all: reported, not held to the bar
-    ("fp32", 0.0, False, 2e-5),
+@pytest.mark.parametrize("prec,fp64_tau,boys64,df32,tol", [
+    ("mixed", 0.0, False, False, 1e-6),    # default split (Q_ab Q_cd >= 3e-2 in FP64): the reduced-precision bar
+    ("mixed", 0.0, False, True, 1e-6),     # the same split in double-float
+    ("mixed", 1e-3, True, False, 1e-6),
+    ("mixed", -1.0, False, False, 2e-5),   # no FP64 quartets at all: reported, not held to the bar
+    ("fp32", 0.0, False, False, 2e-5),
 ])
-def test_jk_reduced_precision_energy(mess, water2_scf, prec, fp64_tau, boys64, tol):
+def test_jk_reduced_precision_energy(mess, water2_scf, prec, fp64_tau, boys64, df32, tol):
     mol, D, Jr, Kr = water2_scf
     g = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
-    J, K, info = g.jk(D, prec=prec, fp64_tau=fp64_tau, boys_fp64=boys64)
+    J, K, info = g.jk(D, prec=prec, fp64_tau=fp64_tau, boys_fp64=boys64, split_df32=df32)
     dE = abs(_two_electron_energy(D, J, K) - _two_electron_energy(D, Jr, Kr))
     assert dE <= tol, dE
     assert np.abs(J - Jr).max() < 1e-4 and np.abs(K - Kr).max() < 1e-4
@@ -113,6 +114,19 @@ def test_jk_reduced_precision_energy(mess, water2_scf, prec, fp64_tau, boys64, t
         assert 0 < info["shell_quartets_fp64"] < info["shell_quartets"]
     else:
         assert info["shell_quartets_fp64"] == 0
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3]], ids=[IDS[1], IDS[2], IDS[3]])
+def test_jk_double_float_every_quartet(mess, oracle_mod, case):
+    """Every quartet above a vanishing split threshold runs in double-float: FP64-class results."""
+    _, mol, basis = case
+    g, o = _pair(mess, oracle_mod, mol, basis)
+    D = mi.random_symmetric_density(g.nbf, 29)
+    J, K, info = g.jk(D, prec="mixed", fp64_tau=1e-300, split_df32=True)
+    assert info["shell_quartets_fp64"] == info["shell_quartets"]
+    Jr, Kr = oracle_mod.jk(o, D)
+    assert np.abs(J - Jr).max() <= 1e-8
+    assert np.abs(K - Kr).max() <= 1e-8
 
 
 def test_jk_device_matches_host(mess):
@@ -165,3 +179,23 @@ def test_single_atom_and_errors(mess, oracle_mod, tmp_path):
     bad.write_text("element H\nS 2\n 1.0 1.0\n")
     with pytest.raises(mess.MessError):
         mess.Basis([1], [[0, 0, 0]], str(bad))
+
+
+def test_full_size_water32_sampled(mess, oracle_mod):
+    """(H2O)_32 / 6-31G* (608 functions), tau = 1e-10, the benchmark's reduced-precision
+    configuration (default split in double-float): sampled elements against the oracle's defining
+    sums, and the whole matrices' symmetry."""
+    mol = mi.water_cluster(32, 19.0, 2006)
+    g = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
+    assert g.nbf == 608
+    D = mi.random_symmetric_density(g.nbf, 2006)
+    J, K, info = g.jk(D, prec="mixed", schwarz_tau=1e-10, split_df32=True)
+    assert info["shell_quartets_fp64"] > 0
+    o = oracle_mod.basis_for(mol, mi.basis_path("6-31gs"))
+    Q = oracle_mod.schwarz(o)
+    rng = np.random.default_rng(32)
+    rows, cols = rng.integers(0, g.nbf, 4), rng.integers(0, g.nbf, 4)
+    Jr, Kr = oracle_mod.jk_elements(o, D, rows, cols, tau=1e-10, Q=Q)
+    assert np.abs(J[rows, cols] - Jr).max() <= 2e-5
+    assert np.abs(K[rows, cols] - Kr).max() <= 2e-5
+    assert np.allclose(J, J.T, atol=0) and np.allclose(K, K.T, atol=0)
