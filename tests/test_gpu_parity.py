@@ -145,6 +145,29 @@ def test_jk_device_matches_host(mess):
     assert np.abs(dK.cpu().numpy() - K).max() < 1e-12
 
 
+@pytest.mark.parametrize("opts", [dict(prec="fp64"), dict(prec="mixed", split_df32=True), dict(prec="fp32")],
+                         ids=["fp64", "mixed_df32", "fp32"])
+def test_jk_device_repeated_builds(mess, opts):
+    """Repeated device builds on the same buffers (replayed as one captured graph from the third call)
+    follow the density's current contents and match one-off host-buffer builds."""
+    import torch
+    mol = mi.water_cluster(2, 9.0, 11)
+    g = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
+    Ds = [mi.random_symmetric_density(g.nbf, 40 + k) for k in range(2)]
+    ref = [g.jk(D, **opts)[:2] for D in Ds]
+    dD = torch.zeros((g.nbf, g.nbf), dtype=torch.float64, device="cuda")
+    dJ, dK = torch.empty_like(dD), torch.empty_like(dD)
+    s = torch.cuda.current_stream()
+    for it in range(6):
+        k = it % 2
+        dD.copy_(torch.from_numpy(Ds[k]))
+        info = g.jk_device(dD, dJ, dK, stream=s, **opts)
+        torch.cuda.synchronize()
+        assert info["function_quartets"] > 0
+        assert np.abs(dJ.cpu().numpy() - ref[k][0]).max() < 1e-11
+        assert np.abs(dK.cpu().numpy() - ref[k][1]).max() < 1e-11
+
+
 def test_full_size_water8_sampled(mess, oracle_mod):
     """(H2O)_8 / 6-31G* (152 functions) at tau = 1e-10: sampled J/K elements against the oracle."""
     mol = mi.water_cluster(8, 12.0, 2002)
