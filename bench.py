@@ -37,6 +37,7 @@ METRIC = "Schwarz-screened ERI quartets/s and SCF molecules/s vs plain FP64, at 
 UNIT = "unique function quartets/s"
 SCHWARZ_TAU = 1e-10
 L2_FLUSH_BYTES = 512 << 20
+MODE_NAMES = {0: "FP64", 1: "FP32 + FP64 Boys", 2: "FP32", 3: "double-float"}
 
 
 def _env_rank():
@@ -179,6 +180,30 @@ def _oracle_rate(mol, basis_path, nelem, seed=7):
     return evals / dt, oracle.num_threads(), dt
 
 
+def _scf_section(mess, args):
+    """SCF molecules/s: one batched SCF (every molecule in the same launches) over seeded linear-alkane
+    conformers, C_nH_2n+2 with n uniform on 1..12 (seed 2003), STO-3G, core-Hamiltonian guess, in the
+    reduced-precision form and in plain FP64 on the same inputs; wall time of the whole call."""
+    import mess_inputs as mi
+    mols = mi.alkane_batch(args.scf_molecules, 1, 12, 2003)
+    bases = [mess.Basis.from_molecule(m, mi.basis_path("sto-3g")) for m in mols]
+    out = {"workload": f"{len(mols)} alkane conformers C_nH_2n+2, n uniform 1..12, seed 2003, STO-3G "
+                       f"({min(b.nbf for b in bases)}-{max(b.nbf for b in bases)} functions), batched SCF"}
+    energies = {}
+    for name, kw in (("mixed", dict(prec="mixed", split_df32=True)), ("fp64", dict(prec="fp64"))):
+        mess.scf_batch(bases[:4], **kw)                       # warm-up: kernels loaded, pools created
+        t0 = time.perf_counter()
+        res, st = mess.scf_batch(bases, **kw)
+        dt = time.perf_counter() - t0
+        energies[name] = [r["E_total"] for r in res]
+        out[name] = {"molecules_per_s": len(bases) / dt, "seconds": dt,
+                     "converged": sum(int(r["converged"]) for r in res),
+                     "mean_iterations": sum(r["iterations"] for r in res) / len(res)}
+    out["max_abs_dE_mixed_vs_fp64_Ha"] = max(abs(a - b) for a, b in zip(energies["mixed"], energies["fp64"]))
+    out["speedup_of_reduced_precision"] = out["mixed"]["molecules_per_s"] / out["fp64"]["molecules_per_s"]
+    return out
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -248,6 +273,10 @@ def run_ours(args):
             tot += e0.elapsed_time(e1)
         return tot, info
 
+    # kernel choice per bin part by timing the candidates (untimed set-up, like the warm-up)
+    tune_kw = dict(prec=args.prec, schwarz_tau=SCHWARZ_TAU, fp64_tau=args.fp64_tau, split_df32=not args.no_df32)
+    torch.cuda.synchronize(dev)
+    tuned = None if args.no_autotune else g.jk_autotune(D, reps=3, **tune_kw)
     for _ in range(args.warmup):
         g.jk_device(dD, dJ, dK, **kw)
     torch.cuda.synchronize(dev)
@@ -269,16 +298,6 @@ def run_ours(args):
     value = world * fnq * args.steps / (max_ms * 1e-3)
     J_mix, K_mix = dJ.cpu().numpy(), dK.cpu().numpy()
 
-    # plain FP64 path on the same input, and the energy error of the reduced-precision path
-    fp64_steps = max(2, min(args.steps, 5))
-    for _ in range(1):
-        g.jk_device(dD, dJ, dK, **dict(kw, prec="fp64", split_df32=False))
-    ms64, info64 = timed(fp64_steps, prec="fp64", split_df32=False)
-    J64, K64 = dJ.cpu().numpy(), dK.cpu().numpy()
-    e2 = lambda J, K: 0.5 * float(np.sum(D * (J - 0.5 * K)))  # noqa: E731
-    dE = e2(J_mix, K_mix) - e2(J64, K64)
-    fp64_rate = info64["function_quartets"] * fp64_steps / (ms64 * 1e-3)
-
     # roofline of the dominant kernel: per-launch CUDA events on the launching stream
     prof = None
     for _ in range(3):
@@ -292,7 +311,8 @@ def run_ours(args):
         p["ms"] = statistics.mean(p["ms"])
     dom = max(prof, key=lambda p: p["ms"])
     fp32_peak, fp64_peak = mess.fma_peak(stream)
-    peak = fp64_peak if (dom["fp64"] and args.no_df32) else fp32_peak
+    dom_fp64_pipe = dom["mode"] == 0
+    peak = fp64_peak if dom_fp64_pipe else fp32_peak
     achieved = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
     tot_flops = sum(p["flops"] for p in prof)
     tot_ms = sum(p["ms"] for p in prof)
@@ -301,7 +321,7 @@ def run_ours(args):
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
-            key = f"{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']}_{'fp64' if dom['fp64'] else 'fp32'}"
+            key = f"{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']}_{MODE_NAMES[dom['mode']]}_G{dom['G']}_t{dom['team']}"
             if tj.get("workload") == args.workload and key in tj.get("kernels", {}):
                 traffic = tj["kernels"][key]
         except Exception:
@@ -311,9 +331,25 @@ def run_ours(args):
     e2e_t = []
     for _ in range(max(2, min(args.steps, 5))):
         t0 = time.perf_counter()
-        g.jk(D, prec=args.prec, schwarz_tau=SCHWARZ_TAU, fp64_tau=args.fp64_tau, split_df32=not args.no_df32)
+        g.jk(D, **tune_kw)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_t)
+
+    # plain FP64 path on the same input (its own bins, also autotuned), and the energy error of the
+    # reduced-precision path
+    fp64_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    if not args.no_autotune:
+        g.jk_autotune(D, prec="fp64", schwarz_tau=SCHWARZ_TAU, reps=2)
+    for _ in range(2):
+        g.jk_device(dD, dJ, dK, **dict(kw, prec="fp64", split_df32=False))
+    ms64, info64 = timed(fp64_steps, prec="fp64", split_df32=False)
+    J64, K64 = dJ.cpu().numpy(), dK.cpu().numpy()
+    e2 = lambda J, K: 0.5 * float(np.sum(D * (J - 0.5 * K)))  # noqa: E731
+    dE = e2(J_mix, K_mix) - e2(J64, K64)
+    fp64_rate = info64["function_quartets"] * fp64_steps / (ms64 * 1e-3)
+
+    scf = _scf_section(mess, args) if args.scf_molecules > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -331,6 +367,7 @@ def run_ours(args):
                    "schwarz_tau": SCHWARZ_TAU, "fp64_tau": args.fp64_tau if args.fp64_tau else 3e-2,
                    "split_arithmetic": "FP64" if args.no_df32 else "double-float (FP32 pairs)",
                    "density": "converged RHF density of the workload", "l2": "flushed (512 MiB write) before every timed step",
+                   "kernel_choice": "autotuned per bin part" if tuned is not None else "fixed rules",
                    "parallelism": f"replicas x{world}"},
         "shell_quartets_per_step": info["shell_quartets"], "function_quartets_per_step": fnq,
         "shell_quartets_fp64_per_step": info["shell_quartets_fp64"],
@@ -341,11 +378,11 @@ def run_ours(args):
         "gpu_launches": int(info["kernel_launches"]) * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"k_jk_{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']} "
-                               f"({('FP64' if args.no_df32 else 'double-float') if dom['fp64'] else 'FP32'})",
+                     "kernel": f"k_jk_{'team_' if dom['team'] else ''}{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']} "
+                               f"({MODE_NAMES[dom['mode']]}, G={dom['G']}, "
+                               f"{'split part' if dom['fp64'] else 'FP32 part'})",
                      "kernel_ms": dom["ms"], "kernel_share": dom["ms"] / tot_ms,
-                     "peak_source": f"measured FMA-chain peak of this GPU "
-                                    f"({'FP64' if (dom['fp64'] and args.no_df32) else 'FP32'})",
+                     "peak_source": f"measured FMA-chain peak of this GPU ({'FP64' if dom_fp64_pipe else 'FP32'})",
                      "whole_build": {"achieved": tot_flops / (tot_ms * 1e-3) / 1e12, "ms": tot_ms}},
         "peaks_measured_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
         "e2e": {"value": fnq / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8},
@@ -353,9 +390,11 @@ def run_ours(args):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if scf:
+        line["scf"] = scf
     if args.breakdown:
-        line["kernels"] = [{k: p[k] for k in ("la", "lb", "lc", "ld", "fp64", "shell_quartets", "primitive_quartets",
-                                             "flops", "ms")} for p in prof]
+        line["kernels"] = [{k: p[k] for k in ("la", "lb", "lc", "ld", "fp64", "G", "team", "mode", "shell_quartets",
+                                             "primitive_quartets", "flops", "ms")} for p in prof]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -377,6 +416,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-df32", action="store_true", help="evaluate the split quartets in FP64 instead of double-float")
     ap.add_argument("--breakdown", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the fixed kernel-choice rules")
+    ap.add_argument("--scf-molecules", dest="scf_molecules", type=int, default=128,
+                    help="alkane conformers of the batched-SCF section (0: skip it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

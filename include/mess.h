@@ -188,6 +188,9 @@ typedef struct {
     double flops;                /* algorithmic flops of the launch (op counts of the recursion, Boys,
                                     contraction, HRR and digestion; an FMA counts as 2) */
     double ms;                   /* launch duration, CUDA events on opts->cuda_stream */
+    int G;                       /* lanes per shell quartet (primitive loop split over G lanes) */
+    int team;                    /* 1: one warp per shell quartet (level-scheduled recursion) */
+    int mode;                    /* arithmetic: 0 FP64, 1 FP32 + FP64 Boys, 2 FP32, 3 double-float */
 } mess_jk_part;
 
 /* Diagnostic: the J/K build of mess_jk_build_device with a CUDA event pair around every kernel
@@ -195,6 +198,18 @@ typedef struct {
  * Errors: as mess_jk_build_device, MESS_EINVAL if max_parts is too small. */
 mess_status mess_jk_profile(const mess_basis* b, const double* dD, double* dJ, double* dK,
                             const mess_jk_opts* opts, mess_jk_part* parts, int max_parts, int* nparts);
+
+/* Kernel autotuner for the quartet bins of these options (the paper has no counterpart: its kernels
+ * come from a tracing compiler).  Each bin part (one shell-quartet class x primitive-count group x
+ * precision) can be computed by several kernels: G = 1, 4 or 8 lanes per quartet, one warp per
+ * quartet, and for the split (large-integral) parts FP64 or double-float arithmetic when
+ * opts->split_df32 allows it.  Every candidate is launched alone on opts->cuda_stream (one untimed
+ * launch, then the minimum of reps timed ones, reps clamped to 1..50) on host density D (nbf x nbf)
+ * and the fastest is kept for later builds with the same options; results are unchanged to
+ * round-off.  The choice is dropped when the bins are rebuilt for other options.  *nchanged
+ * (nullable): parts whose kernel changed.  Allocates 3 nbf^2 doubles of device scratch for the call
+ * and synchronises the stream.  Errors: as mess_jk_build. */
+mess_status mess_jk_autotune(const mess_basis* b, const double* D, const mess_jk_opts* opts, int reps, int* nchanged);
 
 /* Diagnostic (not part of the paper's method): measured CUDA-core FMA throughput of this GPU in
  * TFLOP/s (2 flops per FMA), FP32 and FP64, from independent FMA chains timed with CUDA events on

@@ -29,7 +29,8 @@ EXPORTED = [
     "mess_basis_create", "mess_basis_nbf", "mess_basis_nshell", "mess_basis_nelectron",
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
     "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
-    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_fma_peak", "mess_last_error",
+    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_jk_autotune", "mess_fma_peak",
+    "mess_last_error",
     "mess_mlp_num_params", "mess_mlp_create", "mess_mlp_destroy", "mess_mlp_get_params", "mess_mlp_set_params",
     "mess_mlp_save", "mess_mlp_load", "mess_mlp_features", "mess_mlp_loss_grad", "mess_mlp_train",
     "mess_mlp_predict",
@@ -55,7 +56,8 @@ class mess_jk_part(ctypes.Structure):
     _fields_ = [("qclass", ctypes.c_int), ("la", ctypes.c_int), ("lb", ctypes.c_int), ("lc", ctypes.c_int),
                 ("ld", ctypes.c_int), ("fp64", ctypes.c_int), ("shell_quartets", ctypes.c_longlong),
                 ("primitive_quartets", ctypes.c_longlong), ("function_quartets", ctypes.c_longlong),
-                ("flops", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("ms", ctypes.c_double), ("G", ctypes.c_int), ("team", ctypes.c_int),
+                ("mode", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +117,8 @@ mess_scf_batch = _sig("mess_scf_batch", ctypes.c_int,
 mess_jk_profile = _sig("mess_jk_profile", ctypes.c_int,
                        [_P, _P, _P, _P, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_part), ctypes.c_int,
                         ctypes.POINTER(ctypes.c_int)])
+mess_jk_autotune = _sig("mess_jk_autotune", ctypes.c_int,
+                        [_P, _DP, ctypes.POINTER(mess_jk_opts), ctypes.c_int, ctypes.POINTER(ctypes.c_int)])
 mess_fma_peak = _sig("mess_fma_peak", ctypes.c_int, [_DP, _DP, _P])
 mess_last_error = _sig("mess_last_error", ctypes.c_char_p, [])
 _FP = ctypes.POINTER(ctypes.c_float)
@@ -258,6 +262,16 @@ class Basis:
         _check(mess_jk_build(self._h, _dptr(D), _dptr(J), _dptr(K), ctypes.byref(o), ctypes.byref(info)),
                "mess_jk_build")
         return J, K, info.as_dict()
+
+    def jk_autotune(self, D, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, boys_fp64=False, split_df32=False, reps=3,
+                    stream=None):
+        """Time every kernel variant of each bin part on host density D and keep the fastest for later
+        builds with these options; returns the number of parts whose kernel changed."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64, split_df32)
+        n = ctypes.c_int()
+        _check(mess_jk_autotune(self._h, _dptr(D), ctypes.byref(o), int(reps), ctypes.byref(n)), "mess_jk_autotune")
+        return n.value
 
     def jk_device(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False,
                   split_df32=False):

@@ -885,11 +885,16 @@ def main(outdir):
     # class table (host + device readable)
     tab = ["// Generated by gen_eri.py: do not edit.", "#pragma once", "",
            f"#define MESS_NUM_QCLASS {len(QUARTET_CLASSES)}", "",
-           "typedef struct { int la, lb, lc, ld, L, nint, nacc, nvrr; long vrr_flops, hrr_flops; } mess_qclass_info;",
+           "// straight: straight-line kernels with G = 1, 4, 8 lanes per quartet (else one op-program",
+           "// kernel, G = 1); team: a warp-per-quartet kernel exists",
+           "typedef struct { int la, lb, lc, ld, L, nint, nacc, nvrr; long vrr_flops, hrr_flops; int straight, team; }",
+           "    mess_qclass_info;",
            "static const mess_qclass_info MESS_QCLASS[MESS_NUM_QCLASS] = {"]
     for f in infos:
+        st = 1 if f["mode"] == "straight" else 0
+        tm = 1 if (team_capable(f) or f["mode"] == "program") else 0
         tab.append(f"    {{{f['la']}, {f['lb']}, {f['lc']}, {f['ld']}, {f['L']}, {f['nint']}, {f['nacc']}, "
-                   f"{f['nvrr']}, {f['vrr_flops']}, {f['hrr_flops']}}},")
+                   f"{f['nvrr']}, {f['vrr_flops']}, {f['hrr_flops']}, {st}, {tm}}},")
     tab.append("};")
     text = "\n".join(tab) + "\n"
     path = os.path.join(outdir, "eri_classes.h")

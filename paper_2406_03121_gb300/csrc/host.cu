@@ -225,7 +225,7 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
                 bp.nbra = (int)bra.size() - bp.bra_off;
                 offs.push_back(bp.total);
                 // heavily contracted quartets: split the primitive loop over 8 lanes
-                const bool straight = MESS_QCLASS[bp.qclass].nacc <= 96 && MESS_QCLASS[bp.qclass].nvrr <= 280;
+                const bool straight = MESS_QCLASS[bp.qclass].straight != 0;
                 const double avg = bp.total > 0 ? (double)bp.prim_quartets / (double)bp.total : 0.0;
                 // lanes per quartet: 8 for long primitive loops; 4 for medium loops of parts too small to
                 // fill the GPU one thread per quartet (measured: slower on parts of millions of quartets)
@@ -234,7 +234,7 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
                 // with at least 40 VRR entries (too few quartets to fill the GPU one thread each:
                 // measured better below about 2e6 quartets x VRR entries, worse above)
                 const double work = (double)bp.total * MESS_QCLASS[bp.qclass].nvrr;
-                bp.team = (!straight || (fp64 && MESS_QCLASS[bp.qclass].nvrr >= 40 && bp.G == 1 && work < 2e6)) ? 1 : 0;
+                bp.team = (!straight || (fp64 && MESS_QCLASS[bp.qclass].team && bp.G == 1 && work < 2e6)) ? 1 : 0;
                 if (bp.nbra > 0) B.parts.push_back(bp);
                 else offs.resize(bp.offs_off);
             }
@@ -744,6 +744,15 @@ static void class_flops(int qc, double* per_prim, double* per_shell)
     *per_shell = (double)c.hrr_flops + 12.0 * c.nint;
 }
 
+// kernel arithmetic of a part: the autotuner's choice, else FP64 / double-float for the split parts
+// and FP32 (with or without FP64 Boys) for the others
+static int part_mode(const BinPart& p, const mess_jk_opts& o)
+{
+    if (p.mode >= 0) return p.mode;
+    if (p.fp64) return (o.prec == MESS_MIXED && o.split_df32) ? MESS_MODE_DF32 : MESS_MODE_FP64;
+    return o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32;
+}
+
 // The launches of one J/K build, all on stream s or forked from it onto the pool's streams and
 // joined back: zero J and K, convert D for the reduced-precision parts, one launch per bin part
 // (most expensive first), symmetrise.  With parts != null every launch runs on s between timing
@@ -782,8 +791,7 @@ static mess_status jk_enqueue(mess_basis* b, const mess_jk_opts& o, const double
         const BinPart& p = b->bins.parts[k];
         ClassLaunchArgs a{};
         a.kind = MESS_KIND_JK;
-        a.mode = p.fp64 ? ((o.prec == MESS_MIXED && o.split_df32) ? MESS_MODE_DF32 : MESS_MODE_FP64)
-                        : (o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);
+        a.mode = part_mode(p, o);
         a.G = p.G;
         a.team = p.team;
         a.bin = bin_launch(b, p);
@@ -855,8 +863,9 @@ static cudaGraphExec_t jk_capture(mess_basis* b, const mess_jk_opts& o, const do
     return exec;
 }
 
-static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
-                          mess_jk_info* info, mess_jk_part* parts, int max_parts, int* nparts, bool graphs = true)
+// Argument checks shared by the J/K entry points, and the quartet bins for the options.
+static mess_status jk_prepare(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
+                              mess_jk_opts* out)
 {
     if (!b || !dD || !dJ || !dK) { mess_set_error("null argument"); return MESS_EINVAL; }
     if (dD == dJ || dD == dK || dJ == dK) { mess_set_error("D, J and K must be distinct buffers"); return MESS_EINVAL; }
@@ -872,7 +881,15 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
     if (o.prec == MESS_MIXED) split = tau64 > 0.0 ? 2 : 1;
     else if (o.prec == MESS_FP32) split = 1;
     if (split != 2) tau64 = 0.0;
-    mess_status st = mess_ensure_bins(b, o.schwarz_tau, tau64, split);
+    *out = o;
+    return mess_ensure_bins(b, o.schwarz_tau, tau64, split);
+}
+
+static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
+                          mess_jk_info* info, mess_jk_part* parts, int max_parts, int* nparts, bool graphs = true)
+{
+    mess_jk_opts o{};
+    mess_status st = jk_prepare(b, dD, dJ, dK, opts, &o);
     if (st != MESS_OK) return st;
     if (parts && (int)b->bins.parts.size() > max_parts) {
         mess_set_error("mess_jk_profile: %d launches, max_parts = %d", (int)b->bins.parts.size(), max_parts);
@@ -883,8 +900,9 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
     // previous build on this basis must be done with them first
     bool need32 = false, needdf = false;
     for (const BinPart& p : b->bins.parts) {
-        if (!p.fp64) need32 = true;
-        else if (o.prec == MESS_MIXED && o.split_df32) needdf = true;
+        const int m = part_mode(p, o);
+        if (m == MESS_MODE_FP32 || m == MESS_MODE_MIXED) need32 = true;
+        else if (m == MESS_MODE_DF32) needdf = true;
     }
     if ((need32 && !b->d_D32.p) || (needdf && !b->d_Ddf.p) || ((need32 || needdf) && !b->dconv_free)) {
         mess_set_error("density copies missing");
@@ -911,6 +929,9 @@ static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* d
             r.shell_quartets = p.total;
             r.primitive_quartets = p.prim_quartets;
             r.function_quartets = p.fn_quartets;
+            r.G = p.G;
+            r.team = p.team;
+            r.mode = part_mode(p, o);
             double fp, fs;
             class_flops(p.qclass, &fp, &fs);
             r.flops = fp * (double)p.prim_quartets + fs * (double)p.total;
@@ -992,6 +1013,129 @@ extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, d
 {
     if (!parts || !nparts || max_parts <= 0) { mess_set_error("mess_jk_profile: no output array"); return MESS_EINVAL; }
     return jk_run(const_cast<mess_basis*>(bc), dD, dJ, dK, opts, nullptr, parts, max_parts, nparts);
+}
+
+// Autotuner: for every part of the bins, time each kernel variant that computes it - lanes per
+// quartet G in {1, 4, 8} (straight-line classes), one warp per quartet (classes with that kernel),
+// and for the split parts FP64 or double-float arithmetic (when the options allow double-float) -
+// alone on the stream, and keep the fastest.  The choice lives with the bins (a rebuild of the
+// bins for other options starts from the fixed rules again).
+static mess_status jk_autotune_device(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
+                                      int reps, int* nchanged)
+{
+    mess_jk_opts o{};
+    mess_status st = jk_prepare(b, dD, dJ, dK, opts, &o);
+    if (st != MESS_OK) return st;
+    if (reps < 1) reps = 1;
+    if (reps > 50) reps = 50;
+    cudaStream_t s = (cudaStream_t)o.cuda_stream;
+    if (b->dconv_free) MESS_CUDA_TRY(cudaStreamWaitEvent(s, b->dconv_free, 0));
+    MESS_CUDA_TRY(mess_launch_convert_density(dD, b->d_D32.p, b->d_Ddf.p, b->packed, s));
+    cudaEvent_t e0, e1;
+    MESS_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) { cudaEventDestroy(e0); mess_set_error("%s", cudaGetErrorString(ce)); return MESS_ECUDA; }
+    struct Variant { int G, team, mode; };
+    int changed = 0;
+    mess_status out = MESS_OK;
+    for (BinPart& p : b->bins.parts) {
+        const mess_qclass_info& c = MESS_QCLASS[p.qclass];
+        std::vector<int> modes;
+        if (p.fp64) {
+            modes.push_back(MESS_MODE_FP64);
+            if (o.prec == MESS_MIXED && o.split_df32 && b->d_Ddf.p) modes.push_back(MESS_MODE_DF32);
+        } else {
+            modes.push_back(o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);
+        }
+        std::vector<Variant> cand;
+        for (int m : modes) {
+            if (c.straight) {
+                cand.push_back({1, 0, m});
+                cand.push_back({4, 0, m});
+                cand.push_back({8, 0, m});
+            } else {
+                cand.push_back({1, 0, m});
+            }
+            if (c.team) cand.push_back({1, 1, m});
+        }
+        const Variant before{p.G, p.team, part_mode(p, o)};
+        Variant best = before;
+        float best_ms = 3.4e38f;
+        for (const Variant& v : cand) {
+            ClassLaunchArgs a{};
+            a.kind = MESS_KIND_JK;
+            a.mode = v.mode;
+            a.G = v.G;
+            a.team = v.team;
+            a.bin = bin_launch(b, p);
+            a.P64_ptr = &b->P64;
+            a.P32_ptr = &b->P32;
+            a.Pdf_ptr = &b->Pdf;
+            a.D = dD;
+            a.D32 = b->d_D32.p;
+            a.Ddf = b->d_Ddf.p;
+            a.J = dJ;
+            a.K = dK;
+            a.n = b->nbf;
+            a.stream = s;
+            // one untimed launch (first use of a kernel loads it), then the minimum over reps
+            cudaError_t e = MESS_CLASS_LAUNCHERS[p.qclass](a);
+            float vmin = 3.4e38f;
+            for (int r = 0; e == cudaSuccess && r < reps; ++r) {
+                cudaEventRecord(e0, s);
+                e = MESS_CLASS_LAUNCHERS[p.qclass](a);
+                cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess) vmin = std::min(vmin, ms);
+            }
+            if (e != cudaSuccess) {
+                mess_set_error("autotune launch (class %d): %s", p.qclass, cudaGetErrorString(e));
+                out = MESS_ECUDA;
+                break;
+            }
+            if (vmin < best_ms) { best_ms = vmin; best = v; }
+        }
+        if (out != MESS_OK) break;
+        if (best.G != before.G || best.team != before.team || best.mode != before.mode) ++changed;
+        p.G = best.G;
+        p.team = best.team;
+        p.mode = best.mode;
+        p.tuned = 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // kernels changed: cached graphs of these bins are stale
+    b->bins.generation += 1;
+    mess_free_jk_graphs(b);
+    if (b->dconv_free) cudaEventRecord(b->dconv_free, s);
+    if (nchanged) *nchanged = changed;
+    return out;
+}
+
+extern "C" mess_status mess_jk_autotune(const mess_basis* bc, const double* D, const mess_jk_opts* opts, int reps,
+                                        int* nchanged)
+{
+    if (!bc || !D) { mess_set_error("null argument"); return MESS_EINVAL; }
+    mess_basis* b = const_cast<mess_basis*>(bc);
+    if (b->nmol != 1) { mess_set_error("mess_jk_autotune: single-molecule bases only"); return MESS_EINVAL; }
+    const size_t nn = (size_t)b->nbf * b->nbf;
+    DevBuf<double> d;
+    MESS_CUDA_TRY(d.alloc(3 * nn));
+    mess_jk_opts o{};
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)o.cuda_stream;
+    mess_status st = MESS_OK;
+    cudaError_t e = cudaMemcpyAsync(d.p, D, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        st = jk_autotune_device(b, d.p, d.p + nn, d.p + 2 * nn, &o, reps, nchanged);
+        e = cudaStreamSynchronize(s);
+    }
+    d.free();
+    if (st != MESS_OK) return st;
+    if (e != cudaSuccess) { mess_set_error("jk_autotune: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
+    return MESS_OK;
 }
 
 extern "C" mess_status mess_jk_build(const mess_basis* b, const double* D, double* J, double* K,

@@ -168,6 +168,34 @@ def test_jk_device_repeated_builds(mess, opts):
         assert np.abs(dK.cpu().numpy() - ref[k][1]).max() < 1e-11
 
 
+@pytest.mark.parametrize("prec,df32", [("fp64", False), ("mixed", True), ("fp32", False)])
+def test_jk_autotuned_kernels(mess, oracle_mod, water2_scf, prec, df32):
+    """After the autotuner has picked a kernel per bin part, the build still matches the oracle
+    (FP64: every element to 1e-8; reduced precision: the energy bar), and the profile reports
+    only variants that exist."""
+    import torch
+    mol, D, Jr, Kr = water2_scf
+    g = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
+    kw = dict(prec=prec, split_df32=df32)
+    changed = g.jk_autotune(D, reps=2, **kw)
+    assert changed >= 0
+    J, K, info = g.jk(D, **kw)
+    e = lambda J, K: 0.5 * float(np.sum(D * (J - 0.5 * K)))  # noqa: E731
+    if prec == "fp64":
+        assert np.abs(J - Jr).max() <= 1e-8 and np.abs(K - Kr).max() <= 1e-8
+    else:
+        assert abs(e(J, K) - e(Jr, Kr)) <= (1e-6 if prec == "mixed" else 2e-5)
+    dD = torch.from_numpy(D).cuda()
+    dJ, dK = torch.empty_like(dD), torch.empty_like(dD)
+    parts = g.jk_profile(dD, dJ, dK, **kw)
+    assert len(parts) == info["kernel_launches"] - 1 - (prec != "fp64")
+    for p in parts:
+        assert p["G"] in (1, 4, 8) and p["team"] in (0, 1)
+        assert p["mode"] in ((0, 3) if p["fp64"] and df32 else (0,) if p["fp64"] else (2,))
+        assert not (p["team"] and p["G"] != 1)
+    assert np.abs(dJ.cpu().numpy() - J).max() < 1e-9
+
+
 def test_full_size_water8_sampled(mess, oracle_mod):
     """(H2O)_8 / 6-31G* (152 functions) at tau = 1e-10: sampled J/K elements against the oracle."""
     mol = mi.water_cluster(8, 12.0, 2002)
