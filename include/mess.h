@@ -199,6 +199,17 @@ typedef struct {
 mess_status mess_jk_profile(const mess_basis* b, const double* dD, double* dJ, double* dK,
                             const mess_jk_opts* opts, mess_jk_part* parts, int max_parts, int* nparts);
 
+/* Manual kernel choice for the quartet bins of these options (the paper has no counterpart), e.g. to
+ * test every kernel variant against the oracle: every part of a straight-line class runs with G lanes
+ * per quartet (1, 4, 8 or 32), or one warp per quartet if team != 0 and the class has that kernel;
+ * parts of the op-program classes run one warp per quartet if team != 0, else one thread per quartet.
+ * split_mode: -1 keeps the arithmetic of the split parts, 0 = FP64, 3 = double-float (needs
+ * prec MESS_MIXED and split_df32).  Kept until the bins are rebuilt for other options or the
+ * autotuner runs.  *nchanged (nullable): parts whose kernel changed.  No GPU work.
+ * Errors: MESS_EINVAL (bad arguments). */
+mess_status mess_jk_set_variant(const mess_basis* b, const mess_jk_opts* opts, int G, int team, int split_mode,
+                                int* nchanged);
+
 /* Kernel autotuner for the quartet bins of these options (the paper has no counterpart: its kernels
  * come from a tracing compiler).  Each bin part (one shell-quartet class x primitive-count group x
  * precision) can be computed by several kernels: G = 1, 4 or 8 lanes per quartet, one warp per

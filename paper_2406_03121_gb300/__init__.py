@@ -29,7 +29,8 @@ EXPORTED = [
     "mess_basis_create", "mess_basis_nbf", "mess_basis_nshell", "mess_basis_nelectron",
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
     "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
-    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_jk_autotune", "mess_fma_peak",
+    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_jk_autotune", "mess_jk_set_variant",
+    "mess_fma_peak",
     "mess_last_error",
     "mess_mlp_num_params", "mess_mlp_create", "mess_mlp_destroy", "mess_mlp_get_params", "mess_mlp_set_params",
     "mess_mlp_save", "mess_mlp_load", "mess_mlp_features", "mess_mlp_loss_grad", "mess_mlp_train",
@@ -119,6 +120,9 @@ mess_jk_profile = _sig("mess_jk_profile", ctypes.c_int,
                         ctypes.POINTER(ctypes.c_int)])
 mess_jk_autotune = _sig("mess_jk_autotune", ctypes.c_int,
                         [_P, _DP, ctypes.POINTER(mess_jk_opts), ctypes.c_int, ctypes.POINTER(ctypes.c_int)])
+mess_jk_set_variant = _sig("mess_jk_set_variant", ctypes.c_int,
+                           [_P, ctypes.POINTER(mess_jk_opts), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.POINTER(ctypes.c_int)])
 mess_fma_peak = _sig("mess_fma_peak", ctypes.c_int, [_DP, _DP, _P])
 mess_last_error = _sig("mess_last_error", ctypes.c_char_p, [])
 _FP = ctypes.POINTER(ctypes.c_float)
@@ -271,6 +275,15 @@ class Basis:
         o = jk_opts(prec, schwarz_tau, fp64_tau, stream, boys_fp64, split_df32)
         n = ctypes.c_int()
         _check(mess_jk_autotune(self._h, _dptr(D), ctypes.byref(o), int(reps), ctypes.byref(n)), "mess_jk_autotune")
+        return n.value
+
+    def jk_set_variant(self, G=1, team=False, split_mode=-1, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0,
+                       boys_fp64=False, split_df32=False):
+        """Force one kernel variant on every bin part of these options (see mess_jk_set_variant)."""
+        o = jk_opts(prec, schwarz_tau, fp64_tau, None, boys_fp64, split_df32)
+        n = ctypes.c_int()
+        _check(mess_jk_set_variant(self._h, ctypes.byref(o), int(G), int(bool(team)), int(split_mode),
+                                   ctypes.byref(n)), "mess_jk_set_variant")
         return n.value
 
     def jk_device(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False,

@@ -850,7 +850,7 @@ def main(outdir):
               "            else",
               f"                k_jk_{t}<float, 2, {GG}><<<gg, T, 0, a.stream>>>(a.bin, *a.P32_ptr, dmat<float>(a), a.J, a.K, a.n);",
               "            return cudaGetLastError();",
-              "        }"] for GG in (4, 8)], []) if info["mode"] == "straight" else []) + [
+              "        }"] for GG in (4, 8, 32)], []) if info["mode"] == "straight" else []) + [
               "        if (a.mode == MESS_MODE_FP64)",
               f"            k_jk_{t}<double, 0, 1><<<g, T, 0, a.stream>>>(a.bin, *a.P64_ptr, dmat<double>(a), a.J, a.K, a.n);",
               "        else if (a.mode == MESS_MODE_MIXED)",

@@ -273,7 +273,7 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
 // Per-device pool of non-blocking streams: the class launches of one J/K build fork from the
 // caller's stream, run concurrently (most of them are small), and join back before the
 // symmetrisation.  Fork/join is by events, so a captured caller stream captures the whole build.
-#define MESS_NSTREAMS 8
+#define MESS_NSTREAMS 16
 struct StreamPool {
     bool init = false;
     cudaStream_t s[MESS_NSTREAMS];
@@ -1016,7 +1016,7 @@ extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, d
 }
 
 // Autotuner: for every part of the bins, time each kernel variant that computes it - lanes per
-// quartet G in {1, 4, 8} (straight-line classes), one warp per quartet (classes with that kernel),
+// quartet G in {1, 4, 8, 32} (straight-line classes), one warp per quartet (classes with that kernel),
 // and for the split parts FP64 or double-float arithmetic (when the options allow double-float) -
 // alone on the stream, and keep the fastest.  The choice lives with the bins (a rebuild of the
 // bins for other options starts from the fixed rules again).
@@ -1053,6 +1053,7 @@ static mess_status jk_autotune_device(mess_basis* b, const double* dD, double* d
                 cand.push_back({1, 0, m});
                 cand.push_back({4, 0, m});
                 cand.push_back({8, 0, m});
+                cand.push_back({32, 0, m});
             } else {
                 cand.push_back({1, 0, m});
             }
@@ -1112,6 +1113,41 @@ static mess_status jk_autotune_device(mess_basis* b, const double* dD, double* d
     if (b->dconv_free) cudaEventRecord(b->dconv_free, s);
     if (nchanged) *nchanged = changed;
     return out;
+}
+
+extern "C" mess_status mess_jk_set_variant(const mess_basis* bc, const mess_jk_opts* opts, int G, int team,
+                                           int split_mode, int* nchanged)
+{
+    if (!bc) { mess_set_error("null argument"); return MESS_EINVAL; }
+    if (G != 1 && G != 4 && G != 8 && G != 32) { mess_set_error("G must be 1, 4, 8 or 32"); return MESS_EINVAL; }
+    if (split_mode != -1 && split_mode != MESS_MODE_FP64 && split_mode != MESS_MODE_DF32) {
+        mess_set_error("split_mode must be -1, 0 (FP64) or 3 (double-float)");
+        return MESS_EINVAL;
+    }
+    mess_basis* b = const_cast<mess_basis*>(bc);
+    mess_jk_opts o{};
+    // jk_prepare wants distinct buffer pointers; none is touched here
+    static double dummy[3];
+    mess_status st = jk_prepare(b, dummy, dummy + 1, dummy + 2, opts, &o);
+    if (st != MESS_OK) return st;
+    if (split_mode == MESS_MODE_DF32 && !(o.prec == MESS_MIXED && o.split_df32)) {
+        mess_set_error("double-float split parts need prec MESS_MIXED with split_df32");
+        return MESS_EINVAL;
+    }
+    int changed = 0;
+    for (BinPart& p : b->bins.parts) {
+        const mess_qclass_info& c = MESS_QCLASS[p.qclass];
+        const int G0 = p.G, t0 = p.team, m0 = part_mode(p, o);
+        if (!c.straight) { p.G = 1; p.team = team ? 1 : 0; }          // op-program classes: G = 1 only
+        else if (team && c.team) { p.team = 1; p.G = 1; }
+        else { p.team = 0; p.G = G; }
+        if (p.fp64 && split_mode >= 0) p.mode = split_mode;
+        if (p.G != G0 || p.team != t0 || part_mode(p, o) != m0) ++changed;
+    }
+    b->bins.generation += 1;
+    mess_free_jk_graphs(b);
+    if (nchanged) *nchanged = changed;
+    return MESS_OK;
 }
 
 extern "C" mess_status mess_jk_autotune(const mess_basis* bc, const double* D, const mess_jk_opts* opts, int reps,

@@ -196,6 +196,32 @@ def test_jk_autotuned_kernels(mess, oracle_mod, water2_scf, prec, df32):
     assert np.abs(dJ.cpu().numpy() - J).max() < 1e-9
 
 
+VARIANTS = [(1, False), (4, False), (8, False), (32, False), (1, True)]
+
+
+@pytest.mark.parametrize("G,team", VARIANTS, ids=[f"G{g}{'_team' if t else ''}" for g, t in VARIANTS])
+def test_jk_every_kernel_variant(mess, oracle_mod, G, team):
+    """Each kernel variant (lanes per quartet, warp per quartet) on every class of a water dimer in
+    6-31G*: FP64, and double-float on every quartet, against the oracle to 1e-8; FP32 on every
+    quartet within the reduced-precision energy tolerance of the unsplit form."""
+    mol = mi.water_cluster(2, 9.0, 11)
+    g, o = _pair(mess, oracle_mod, mol, "6-31gs")
+    D = mi.random_symmetric_density(g.nbf, 31)
+    Jr, Kr = oracle_mod.jk(o, D)
+    e = lambda J, K: 0.5 * float(np.sum(D * (J - 0.5 * K)))  # noqa: E731
+    for kw, split_mode, tol in ((dict(prec="fp64"), -1, 1e-8),
+                                (dict(prec="mixed", fp64_tau=1e-300, split_df32=True), 3, 1e-8),
+                                (dict(prec="mixed", fp64_tau=1e-300, split_df32=True), 0, 1e-8),
+                                (dict(prec="mixed", fp64_tau=-1.0), -1, None)):
+        g.jk_set_variant(G=G, team=team, split_mode=split_mode, **kw)
+        J, K, info = g.jk(D, **kw)
+        if tol is not None:
+            assert np.abs(J - Jr).max() <= tol, (kw, split_mode)
+            assert np.abs(K - Kr).max() <= tol, (kw, split_mode)
+        else:
+            assert abs(e(J, K) - e(Jr, Kr)) <= 2e-5
+
+
 def test_full_size_water8_sampled(mess, oracle_mod):
     """(H2O)_8 / 6-31G* (152 functions) at tau = 1e-10: sampled J/K elements against the oracle."""
     mol = mi.water_cluster(8, 12.0, 2002)
