@@ -189,7 +189,8 @@ typedef struct {
                                     contraction, HRR and digestion; an FMA counts as 2) */
     double ms;                   /* launch duration, CUDA events on opts->cuda_stream */
     int G;                       /* lanes per shell quartet (primitive loop split over G lanes) */
-    int team;                    /* 1: one warp per shell quartet (level-scheduled recursion) */
+    int team;                    /* 1: one warp per shell quartet (level-scheduled recursion), 2: one
+                                    block of 4 warps per quartet, 0: G lanes per quartet */
     int mode;                    /* arithmetic: 0 FP64, 1 FP32 + FP64 Boys, 2 FP32, 3 double-float */
 } mess_jk_part;
 
@@ -201,8 +202,9 @@ mess_status mess_jk_profile(const mess_basis* b, const double* dD, double* dJ, d
 
 /* Manual kernel choice for the quartet bins of these options (the paper has no counterpart), e.g. to
  * test every kernel variant against the oracle: every part of a straight-line class runs with G lanes
- * per quartet (1, 4, 8 or 32), or one warp per quartet if team != 0 and the class has that kernel;
- * parts of the op-program classes run one warp per quartet if team != 0, else one thread per quartet.
+ * per quartet (1, 4, 8 or 32), or one warp (team = 1) or one block of 4 warps (team = 2) per quartet
+ * if the class has that kernel; parts of the op-program classes run one warp or block per quartet if
+ * team != 0, else one thread per quartet.
  * split_mode: -1 keeps the arithmetic of the split parts, 0 = FP64, 3 = double-float (needs
  * prec MESS_MIXED and split_df32).  Kept until the bins are rebuilt for other options or the
  * autotuner runs.  *nchanged (nullable): parts whose kernel changed.  No GPU work.
@@ -212,9 +214,9 @@ mess_status mess_jk_set_variant(const mess_basis* b, const mess_jk_opts* opts, i
 
 /* Kernel autotuner for the quartet bins of these options (the paper has no counterpart: its kernels
  * come from a tracing compiler).  Each bin part (one shell-quartet class x primitive-count group x
- * precision) can be computed by several kernels: G = 1, 4 or 8 lanes per quartet, one warp per
- * quartet, and for the split (large-integral) parts FP64 or double-float arithmetic when
- * opts->split_df32 allows it.  Every candidate is launched alone on opts->cuda_stream (one untimed
+ * precision) can be computed by several kernels: G = 1, 4, 8 or 32 lanes per quartet, one warp per
+ * quartet, one block of 4 warps per quartet, and for the split (large-integral) parts FP64 or
+ * double-float arithmetic when opts->split_df32 allows it.  Every candidate is launched alone on opts->cuda_stream (one untimed
  * launch, then the minimum of reps timed ones, reps clamped to 1..50) on host density D (nbf x nbf)
  * and the fastest is kept for later builds with the same options; results are unchanged to
  * round-off.  The choice is dropped when the bins are rebuilt for other options.  *nchanged

@@ -277,12 +277,12 @@ class Basis:
         _check(mess_jk_autotune(self._h, _dptr(D), ctypes.byref(o), int(reps), ctypes.byref(n)), "mess_jk_autotune")
         return n.value
 
-    def jk_set_variant(self, G=1, team=False, split_mode=-1, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0,
+    def jk_set_variant(self, G=1, team=0, split_mode=-1, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0,
                        boys_fp64=False, split_df32=False):
         """Force one kernel variant on every bin part of these options (see mess_jk_set_variant)."""
         o = jk_opts(prec, schwarz_tau, fp64_tau, None, boys_fp64, split_df32)
         n = ctypes.c_int()
-        _check(mess_jk_set_variant(self._h, ctypes.byref(o), int(G), int(bool(team)), int(split_mode),
+        _check(mess_jk_set_variant(self._h, ctypes.byref(o), int(G), int(team), int(split_mode),
                                    ctypes.byref(n)), "mess_jk_set_variant")
         return n.value
 

@@ -572,7 +572,15 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
 // memory, __syncwarp between levels), then split the digestion outputs between them.
 // ------------------------------------------------------------------------------------------
 
-template <typename R, int BMODE, int L, int NVI, int NH, int NACC, int NVL, int NHL, int NINT,
+// TW threads share one shell quartet: 32 (a warp, MESS_TEAM_WARPS quartets per block) or
+// 32 * MESS_TEAM_WARPS (the whole block on one quartet, for parts with very few quartets)
+template <int TW> __device__ __forceinline__ void team_sync()
+{
+    if (TW == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <typename R, int BMODE, int TW, int L, int NVI, int NH, int NACC, int NVL, int NHL, int NINT,
           int NA, int NB, int NC, int ND>
 __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable<R>& P, const typename DElem<R>::T* __restrict__ D,
                                              double* __restrict__ J, double* __restrict__ K, int n,
@@ -582,16 +590,17 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
                                              const float* __restrict__ fscale_hi, const float* __restrict__ fscale_lo,
                                              R* __restrict__ sm)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long q = (long long)blockIdx.x * MESS_TEAM_WARPS + warp;
-    if (q >= b.total) return;                       // whole warp leaves together
-    R* V = sm + (size_t)warp * (NVI + NH);
+    static_assert(TW == 32 || TW == 32 * MESS_TEAM_WARPS, "a warp or the whole block per quartet");
+    const int slot = threadIdx.x / TW, lane = threadIdx.x % TW;
+    const long long q = (long long)blockIdx.x * (32 * MESS_TEAM_WARPS / TW) + slot;
+    if (q >= b.total) return;                       // the quartet's threads leave together
+    R* V = sm + (size_t)slot * (NVI + NH);
     R* H = V + NVI;
     const int i = find_bra(b.offs, b.nbra, q);
     const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));
     const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);
-    for (int k = lane; k < NACC; k += 32) H[k] = R(0);
-    __syncwarp();
+    for (int k = lane; k < NACC; k += TW) H[k] = R(0);
+    team_sync<TW>();
     const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];
     const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
     const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);
@@ -616,7 +625,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
             for (int lv = 0; lv < NVL; ++lv) {
                 const int oend = __ldg(vlev + lv + 1);
 #pragma unroll 1
-                for (int o = __ldg(vlev + lv) + lane; o < oend; o += 32) {
+                for (int o = __ldg(vlev + lv) + lane; o < oend; o += TW) {
                     const uint4 w = __ldg(vprog + o);
                     const int kind = w.x & 3, d = (w.x >> 2) & 3;
                     const int m1 = (w.x >> 4) & 15, m2 = (w.x >> 8) & 15, t = w.x >> 16;
@@ -639,7 +648,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
                         V[t] = v;
                     }
                 }
-                __syncwarp();
+                team_sync<TW>();
             }
         }
     }
@@ -649,16 +658,16 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     for (int lv = 0; lv < NHL; ++lv) {
         const int oend = __ldg(hlev + lv + 1);
 #pragma unroll 1
-        for (int o = __ldg(hlev + lv) + lane; o < oend; o += 32) {
+        for (int o = __ldg(hlev + lv) + lane; o < oend; o += TW) {
             const uint2 w = __ldg(hprog + o);
             const int t = w.x & 0xffff, d = (w.x >> 16) & 3, side = (w.x >> 18) & 1;
             const R X = side ? pick3(d, CDx, CDy, CDz) : pick3(d, ABx, ABy, ABz);
             H[t] = H[w.y & 0xffff] + X * H[w.y >> 16];
         }
-        __syncwarp();
+        team_sync<TW>();
     }
-    for (int k = lane; k < NINT; k += 32) V[k] = gen_scale<R>(fscale, fscale_hi, fscale_lo, k) * H[__ldg(fslot + k)];
-    __syncwarp();
+    for (int k = lane; k < NINT; k += TW) V[k] = gen_scale<R>(fscale, fscale_hi, fscale_lo, k) * H[__ldg(fslot + k)];
+    team_sync<TW>();
     const R* I = V;
     R s = R(1);
     if (__ldg(P.same + bp)) s *= R(0.5);
@@ -673,42 +682,42 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     const size_t nn = (size_t)__ldg(P.mn + mol_);
     (void)n;
 #define MESS_I(a_, b_, c_, d_) I[(((a_) * NB + (b_)) * NC + (c_)) * ND + (d_)]
-    for (int o = lane; o < NA * NB; o += 32) {          // J_ab = sum_cd I D_cd
+    for (int o = lane; o < NA * NB; o += TW) {          // J_ab = sum_cd I D_cd
         const int a = o / NB, bb = o % NB;
         R t = R(0);
         for (int c = 0; c < NC; ++c)
             for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD(D + (fc + c) * nn + fd + d);
         atomicAdd(J + (fa + a) * nn + fb + bb, to_f64(s * t));
     }
-    for (int o = lane; o < NC * ND; o += 32) {          // J_cd = sum_ab I D_ab
+    for (int o = lane; o < NC * ND; o += TW) {          // J_cd = sum_ab I D_ab
         const int c = o / ND, d = o % ND;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
             for (int bb = 0; bb < NB; ++bb) t += MESS_I(a, bb, c, d) * ldD(D + (fa + a) * nn + fb + bb);
         atomicAdd(J + (fc + c) * nn + fd + d, to_f64(s * t));
     }
-    for (int o = lane; o < NA * NC; o += 32) {          // K_ac = sum_bd I D_bd
+    for (int o = lane; o < NA * NC; o += TW) {          // K_ac = sum_bd I D_bd
         const int a = o / NC, c = o % NC;
         R t = R(0);
         for (int bb = 0; bb < NB; ++bb)
             for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD(D + (fb + bb) * nn + fd + d);
         atomicAdd(K + (fa + a) * nn + fc + c, to_f64(s * t));
     }
-    for (int o = lane; o < NA * ND; o += 32) {          // K_ad = sum_bc I D_bc
+    for (int o = lane; o < NA * ND; o += TW) {          // K_ad = sum_bc I D_bc
         const int a = o / ND, d = o % ND;
         R t = R(0);
         for (int bb = 0; bb < NB; ++bb)
             for (int c = 0; c < NC; ++c) t += MESS_I(a, bb, c, d) * ldD(D + (fb + bb) * nn + fc + c);
         atomicAdd(K + (fa + a) * nn + fd + d, to_f64(s * t));
     }
-    for (int o = lane; o < NB * NC; o += 32) {          // K_bc = sum_ad I D_ad
+    for (int o = lane; o < NB * NC; o += TW) {          // K_bc = sum_ad I D_ad
         const int bb = o / NC, c = o % NC;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
             for (int d = 0; d < ND; ++d) t += MESS_I(a, bb, c, d) * ldD(D + (fa + a) * nn + fd + d);
         atomicAdd(K + (fb + bb) * nn + fc + c, to_f64(s * t));
     }
-    for (int o = lane; o < NB * ND; o += 32) {          // K_bd = sum_ac I D_ac
+    for (int o = lane; o < NB * ND; o += TW) {          // K_bd = sum_ac I D_ac
         const int bb = o / ND, d = o % ND;
         R t = R(0);
         for (int a = 0; a < NA; ++a)
@@ -723,13 +732,13 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     {                                                                                               \
         return team_smem_bytes<R, __VA_ARGS__>();                                                   \
     }                                                                                               \
-    template <typename R, int BMODE>                                                                \
+    template <typename R, int BMODE, int TW>                                                        \
     __global__ void __launch_bounds__(32 * MESS_TEAM_WARPS)                                         \
     k_jk_team_##TAG(const BinLaunch b, const PairTable<R> P, const typename DElem<R>::T* __restrict__ D,          \
                     double* __restrict__ J, double* __restrict__ K, int n)                          \
     {                                                                                               \
         extern __shared__ __align__(16) unsigned char mess_team_smem[];                             \
-        jk_team_body<R, BMODE, __VA_ARGS__>(b, P, D, J, K, n, MESS_TEAM_PROG_##TAG,                 \
+        jk_team_body<R, BMODE, TW, __VA_ARGS__>(b, P, D, J, K, n, MESS_TEAM_PROG_##TAG,             \
                                             reinterpret_cast<R*>(mess_team_smem));                  \
     }
 #define MESS_DEFINE_TEAM_KERNEL(TAG) MESS_DEFINE_TEAM_KERNEL_IMPL(TAG, MESS_TEAM_ARGS_##TAG)

@@ -1016,7 +1016,8 @@ extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, d
 }
 
 // Autotuner: for every part of the bins, time each kernel variant that computes it - lanes per
-// quartet G in {1, 4, 8, 32} (straight-line classes), one warp per quartet (classes with that kernel),
+// quartet G in {1, 4, 8, 32} (straight-line classes), one warp or one block of MESS_TEAM_WARPS warps per
+// quartet (classes with that kernel),
 // and for the split parts FP64 or double-float arithmetic (when the options allow double-float) -
 // alone on the stream, and keep the fastest.  The choice lives with the bins (a rebuild of the
 // bins for other options starts from the fixed rules again).
@@ -1057,7 +1058,10 @@ static mess_status jk_autotune_device(mess_basis* b, const double* dD, double* d
             } else {
                 cand.push_back({1, 0, m});
             }
-            if (c.team) cand.push_back({1, 1, m});
+            if (c.team) {
+                cand.push_back({1, 1, m});
+                cand.push_back({1, 2, m});
+            }
         }
         const Variant before{p.G, p.team, part_mode(p, o)};
         Variant best = before;
@@ -1120,6 +1124,7 @@ extern "C" mess_status mess_jk_set_variant(const mess_basis* bc, const mess_jk_o
 {
     if (!bc) { mess_set_error("null argument"); return MESS_EINVAL; }
     if (G != 1 && G != 4 && G != 8 && G != 32) { mess_set_error("G must be 1, 4, 8 or 32"); return MESS_EINVAL; }
+    if (team < 0 || team > 2) { mess_set_error("team must be 0, 1 or 2"); return MESS_EINVAL; }
     if (split_mode != -1 && split_mode != MESS_MODE_FP64 && split_mode != MESS_MODE_DF32) {
         mess_set_error("split_mode must be -1, 0 (FP64) or 3 (double-float)");
         return MESS_EINVAL;
@@ -1138,8 +1143,8 @@ extern "C" mess_status mess_jk_set_variant(const mess_basis* bc, const mess_jk_o
     for (BinPart& p : b->bins.parts) {
         const mess_qclass_info& c = MESS_QCLASS[p.qclass];
         const int G0 = p.G, t0 = p.team, m0 = part_mode(p, o);
-        if (!c.straight) { p.G = 1; p.team = team ? 1 : 0; }          // op-program classes: G = 1 only
-        else if (team && c.team) { p.team = 1; p.G = 1; }
+        if (!c.straight) { p.G = 1; p.team = team; }                  // op-program classes: G = 1 only
+        else if (team && c.team) { p.team = team; p.G = 1; }
         else { p.team = 0; p.G = G; }
         if (p.fp64 && split_mode >= 0) p.mode = split_mode;
         if (p.G != G0 || p.team != t0 || part_mode(p, o) != m0) ++changed;

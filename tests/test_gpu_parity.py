@@ -190,18 +190,18 @@ def test_jk_autotuned_kernels(mess, oracle_mod, water2_scf, prec, df32):
     parts = g.jk_profile(dD, dJ, dK, **kw)
     assert len(parts) == info["kernel_launches"] - 1 - (prec != "fp64")
     for p in parts:
-        assert p["G"] in (1, 4, 8, 32) and p["team"] in (0, 1)
+        assert p["G"] in (1, 4, 8, 32) and p["team"] in (0, 1, 2)
         assert p["mode"] in ((0, 3) if p["fp64"] and df32 else (0,) if p["fp64"] else (2,))
         assert not (p["team"] and p["G"] != 1)
     assert np.abs(dJ.cpu().numpy() - J).max() < 1e-9
 
 
-VARIANTS = [(1, False), (4, False), (8, False), (32, False), (1, True)]
+VARIANTS = [(1, 0), (4, 0), (8, 0), (32, 0), (1, 1), (1, 2)]
 
 
-@pytest.mark.parametrize("G,team", VARIANTS, ids=[f"G{g}{'_team' if t else ''}" for g, t in VARIANTS])
+@pytest.mark.parametrize("G,team", VARIANTS, ids=[f"G{g}_team{t}" for g, t in VARIANTS])
 def test_jk_every_kernel_variant(mess, oracle_mod, G, team):
-    """Each kernel variant (lanes per quartet, warp per quartet) on every class of a water dimer in
+    """Each kernel variant (lanes per quartet, warp or block per quartet) on every class of a water dimer in
     6-31G*: FP64, and double-float on every quartet, against the oracle to 1e-8; FP32 on every
     quartet within the reduced-precision energy tolerance of the unsplit form."""
     mol = mi.water_cluster(2, 9.0, 11)
