@@ -200,6 +200,11 @@ typedef struct {
 mess_status mess_jk_profile(const mess_basis* b, const double* dD, double* dJ, double* dK,
                             const mess_jk_opts* opts, mess_jk_part* parts, int max_parts, int* nparts);
 
+/* Diagnostic (not part of the paper's method): marks the start (on != 0) or end of the region a
+ * kernel profiler started with profiling off at launch (ncu --profile-from-start off) records, so
+ * that set-up work (autotuning, warm-up) stays out of a capture.  Errors: MESS_ECUDA. */
+mess_status mess_profiler_range(int on);
+
 /* Manual kernel choice for the quartet bins of these options (the paper has no counterpart), e.g. to
  * test every kernel variant against the oracle: every part of a straight-line class runs with G lanes
  * per quartet (1, 4, 8 or 32), or one warp (team = 1) or one block of 4 warps (team = 2) per quartet
@@ -216,9 +221,11 @@ mess_status mess_jk_set_variant(const mess_basis* b, const mess_jk_opts* opts, i
  * come from a tracing compiler).  Each bin part (one shell-quartet class x primitive-count group x
  * precision) can be computed by several kernels: G = 1, 4, 8 or 32 lanes per quartet, one warp per
  * quartet, one block of 4 warps per quartet, and for the split (large-integral) parts FP64 or
- * double-float arithmetic when opts->split_df32 allows it.  Every candidate is launched alone on opts->cuda_stream (one untimed
- * launch, then the minimum of reps timed ones, reps clamped to 1..50) on host density D (nbf x nbf)
- * and the fastest is kept for later builds with the same options; results are unchanged to
+ * double-float arithmetic when opts->split_df32 allows it.  Each candidate runs on host density D
+ * (nbf x nbf): one untimed launch, then reps timings (clamped to 1..50) of 8 copies launched together
+ * on the library's streams, forked from and joined to opts->cuda_stream - the parts of a build run
+ * concurrently, so a variant is charged for the share of the GPU it takes as well as for its
+ * latency - and the fastest is kept for later builds with the same options; results are unchanged to
  * round-off.  The choice is dropped when the bins are rebuilt for other options.  *nchanged
  * (nullable): parts whose kernel changed.  Allocates 3 nbf^2 doubles of device scratch for the call
  * and synchronises the stream.  Errors: as mess_jk_build. */

@@ -30,7 +30,7 @@ EXPORTED = [
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
     "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
     "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_jk_autotune", "mess_jk_set_variant",
-    "mess_fma_peak",
+    "mess_profiler_range", "mess_fma_peak",
     "mess_last_error",
     "mess_mlp_num_params", "mess_mlp_create", "mess_mlp_destroy", "mess_mlp_get_params", "mess_mlp_set_params",
     "mess_mlp_save", "mess_mlp_load", "mess_mlp_features", "mess_mlp_loss_grad", "mess_mlp_train",
@@ -123,6 +123,7 @@ mess_jk_autotune = _sig("mess_jk_autotune", ctypes.c_int,
 mess_jk_set_variant = _sig("mess_jk_set_variant", ctypes.c_int,
                            [_P, ctypes.POINTER(mess_jk_opts), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.POINTER(ctypes.c_int)])
+mess_profiler_range = _sig("mess_profiler_range", ctypes.c_int, [ctypes.c_int])
 mess_fma_peak = _sig("mess_fma_peak", ctypes.c_int, [_DP, _DP, _P])
 mess_last_error = _sig("mess_last_error", ctypes.c_char_p, [])
 _FP = ctypes.POINTER(ctypes.c_float)
@@ -319,6 +320,11 @@ class Basis:
         out["status"] = st
         out["D"] = D
         return out
+
+
+def profiler_range(on):
+    """Start (True) or stop (False) the region recorded by a profiler launched with profiling off."""
+    _check(mess_profiler_range(int(bool(on))), "mess_profiler_range")
 
 
 def fma_peak(stream=None):

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_profiler_api.h>
+
 #include "mess_internal.h"
 
 // ------------------------------------------------------------------------------------------ errors
@@ -274,6 +276,7 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
 // caller's stream, run concurrently (most of them are small), and join back before the
 // symmetrisation.  Fork/join is by events, so a captured caller stream captures the whole build.
 #define MESS_NSTREAMS 16
+#define MESS_TUNE_COPIES 8   // concurrent copies of a candidate kernel timed by the autotuner
 struct StreamPool {
     bool init = false;
     cudaStream_t s[MESS_NSTREAMS];
@@ -1015,7 +1018,8 @@ extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, d
     return jk_run(const_cast<mess_basis*>(bc), dD, dJ, dK, opts, nullptr, parts, max_parts, nparts);
 }
 
-// Autotuner: for every part of the bins, time each kernel variant that computes it - lanes per
+// Autotuner: for every part of the bins, time each kernel variant that computes it (several copies
+// at once, see below) - lanes per
 // quartet G in {1, 4, 8, 32} (straight-line classes), one warp or one block of MESS_TEAM_WARPS warps per
 // quartet (classes with that kernel),
 // and for the split parts FP64 or double-float arithmetic (when the options allow double-float) -
@@ -1032,6 +1036,9 @@ static mess_status jk_autotune_device(mess_basis* b, const double* dD, double* d
     cudaStream_t s = (cudaStream_t)o.cuda_stream;
     if (b->dconv_free) MESS_CUDA_TRY(cudaStreamWaitEvent(s, b->dconv_free, 0));
     MESS_CUDA_TRY(mess_launch_convert_density(dD, b->d_D32.p, b->d_Ddf.p, b->packed, s));
+    StreamPool* pool = nullptr;
+    MESS_CUDA_TRY(get_pool(&pool));
+    std::unique_lock<std::mutex> lk(pool->mu);
     cudaEvent_t e0, e1;
     MESS_CUDA_TRY(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -1083,12 +1090,24 @@ static mess_status jk_autotune_device(mess_basis* b, const double* dD, double* d
             a.K = dK;
             a.n = b->nbf;
             a.stream = s;
-            // one untimed launch (first use of a kernel loads it), then the minimum over reps
+            // one untimed launch (first use of a kernel loads it), then the minimum over reps of the
+            // time for MESS_TUNE_COPIES copies launched together on the pool's streams: the parts of
+            // a build run concurrently, so a variant is charged for the GPU it occupies as well as
+            // for its latency (a lane split that only fills idle SMs costs nothing extra; one that
+            // crowds out the other parts does)
+            a.stream = s;
             cudaError_t e = MESS_CLASS_LAUNCHERS[p.qclass](a);
             float vmin = 3.4e38f;
             for (int r = 0; e == cudaSuccess && r < reps; ++r) {
                 cudaEventRecord(e0, s);
-                e = MESS_CLASS_LAUNCHERS[p.qclass](a);
+                cudaEventRecord(pool->fork, s);
+                for (int c = 0; e == cudaSuccess && c < MESS_TUNE_COPIES; ++c) {
+                    cudaStreamWaitEvent(pool->s[c], pool->fork, 0);
+                    a.stream = pool->s[c];
+                    e = MESS_CLASS_LAUNCHERS[p.qclass](a);
+                    cudaEventRecord(pool->join[c], pool->s[c]);
+                    cudaStreamWaitEvent(s, pool->join[c], 0);
+                }
                 cudaEventRecord(e1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -1232,5 +1251,12 @@ extern "C" mess_status mess_eri_tensor(const mess_basis* bc, double* G)
     if (e == cudaSuccess) e = cudaMemcpy(G, d.p, n4 * sizeof(double), cudaMemcpyDeviceToHost);
     d.free();
     if (e != cudaSuccess) { mess_set_error("eri_tensor: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
+    return MESS_OK;
+}
+
+extern "C" mess_status mess_profiler_range(int on)
+{
+    const cudaError_t e = on ? cudaProfilerStart() : cudaProfilerStop();
+    if (e != cudaSuccess) { mess_set_error("profiler range: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
     return MESS_OK;
 }

@@ -8,8 +8,9 @@ The workloads and options are those of the J/K benchmark: (H2O)_8 (seed 2002, 12
 (H2O)_32 (seed 2006, 19-bohr cube), 6-31G*, Schwarz threshold 1e-10, split quartets in
 double-float unless --no-df32, kernel choice autotuned unless --no-autotune.  The density is a
 seeded symmetric positive semidefinite matrix: screening uses only the Schwarz factors, so the
-launches (classes, parts, grid sizes) are those of any density.  Prints one line per step with the
-host wall time of the call.
+launches (classes, parts, grid sizes) are those of any density.  The timed steps are bracketed by a
+profiler range (ncu --profile-from-start off records only them, not the autotuning and warm-up).
+Prints one line per step with the host wall time of the call.
 """
 from __future__ import annotations
 
@@ -42,11 +43,13 @@ def main(argv=None):
         print(f"autotune: {changed} parts changed", flush=True)
     for _ in range(args.warmup):
         g.jk(D, **kw)
+    mess.profiler_range(True)          # a profiler started with --profile-from-start off records from here
     for k in range(args.steps):
         t0 = time.perf_counter()
         _, _, info = g.jk(D, **kw)
         print(f"step {k}: {1e3 * (time.perf_counter() - t0):.3f} ms, {info['kernel_launches']} launches, "
               f"{info['function_quartets']} function quartets", flush=True)
+    mess.profiler_range(False)
     return 0
 
 
