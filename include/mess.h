@@ -200,6 +200,16 @@ typedef struct {
 mess_status mess_jk_profile(const mess_basis* b, const double* dD, double* dJ, double* dK,
                             const mess_jk_opts* opts, mess_jk_part* parts, int max_parts, int* nparts);
 
+/* The kernel choice of the quartet bins for these options (the paper has no counterpart), so that one
+ * process's autotuning can be reused by another (a profiling run, whose own timings the profiler
+ * distorts): 4 ints per bin part - quartet class, G, team, arithmetic (0 FP64, 1 FP32 + FP64 Boys,
+ * 2 FP32, 3 double-float).  get: *nparts = number of parts; table (nullable) receives them if
+ * max_parts suffices (else MESS_EINVAL).  set: nparts must equal the parts of the same basis and
+ * options, and every entry must be a kernel that exists for its part (else MESS_EINVAL, nothing
+ * changed).  No GPU work. */
+mess_status mess_jk_get_tuning(const mess_basis* b, const mess_jk_opts* opts, int* table, int max_parts, int* nparts);
+mess_status mess_jk_set_tuning(const mess_basis* b, const mess_jk_opts* opts, const int* table, int nparts);
+
 /* Diagnostic (not part of the paper's method): marks the start (on != 0) or end of the region a
  * kernel profiler started with profiling off at launch (ncu --profile-from-start off) records, so
  * that set-up work (autotuning, warm-up) stays out of a capture.  Errors: MESS_ECUDA. */

@@ -30,7 +30,7 @@ EXPORTED = [
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
     "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
     "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_jk_autotune", "mess_jk_set_variant",
-    "mess_profiler_range", "mess_fma_peak",
+    "mess_jk_get_tuning", "mess_jk_set_tuning", "mess_profiler_range", "mess_fma_peak",
     "mess_last_error",
     "mess_mlp_num_params", "mess_mlp_create", "mess_mlp_destroy", "mess_mlp_get_params", "mess_mlp_set_params",
     "mess_mlp_save", "mess_mlp_load", "mess_mlp_features", "mess_mlp_loss_grad", "mess_mlp_train",
@@ -123,6 +123,9 @@ mess_jk_autotune = _sig("mess_jk_autotune", ctypes.c_int,
 mess_jk_set_variant = _sig("mess_jk_set_variant", ctypes.c_int,
                            [_P, ctypes.POINTER(mess_jk_opts), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.POINTER(ctypes.c_int)])
+mess_jk_get_tuning = _sig("mess_jk_get_tuning", ctypes.c_int,
+                          [_P, ctypes.POINTER(mess_jk_opts), _IP, ctypes.c_int, _IP])
+mess_jk_set_tuning = _sig("mess_jk_set_tuning", ctypes.c_int, [_P, ctypes.POINTER(mess_jk_opts), _IP, ctypes.c_int])
 mess_profiler_range = _sig("mess_profiler_range", ctypes.c_int, [ctypes.c_int])
 mess_fma_peak = _sig("mess_fma_peak", ctypes.c_int, [_DP, _DP, _P])
 mess_last_error = _sig("mess_last_error", ctypes.c_char_p, [])
@@ -286,6 +289,22 @@ class Basis:
         _check(mess_jk_set_variant(self._h, ctypes.byref(o), int(G), int(team), int(split_mode),
                                    ctypes.byref(n)), "mess_jk_set_variant")
         return n.value
+
+    def jk_tuning(self, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, boys_fp64=False, split_df32=False):
+        """Kernel choice per bin part: a list of [class, G, team, arithmetic]."""
+        o = jk_opts(prec, schwarz_tau, fp64_tau, None, boys_fp64, split_df32)
+        n = ctypes.c_int()
+        _check(mess_jk_get_tuning(self._h, ctypes.byref(o), None, 0, ctypes.byref(n)), "mess_jk_get_tuning")
+        t = np.zeros(4 * n.value, dtype=np.int32)
+        _check(mess_jk_get_tuning(self._h, ctypes.byref(o), t.ctypes.data_as(_IP), n.value, ctypes.byref(n)),
+               "mess_jk_get_tuning")
+        return t.reshape(-1, 4).tolist()
+
+    def jk_set_tuning(self, table, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, boys_fp64=False, split_df32=False):
+        """Restore a kernel choice saved by jk_tuning (same basis and options)."""
+        o = jk_opts(prec, schwarz_tau, fp64_tau, None, boys_fp64, split_df32)
+        t = np.ascontiguousarray(np.asarray(table, dtype=np.int32).reshape(-1))
+        _check(mess_jk_set_tuning(self._h, ctypes.byref(o), t.ctypes.data_as(_IP), len(t) // 4), "mess_jk_set_tuning")
 
     def jk_device(self, D, J, K, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, stream=None, boys_fp64=False,
                   split_df32=False):

@@ -1174,6 +1174,67 @@ extern "C" mess_status mess_jk_set_variant(const mess_basis* bc, const mess_jk_o
     return MESS_OK;
 }
 
+// The kernel choice of every part of the bins for these options, as 4 ints per part: quartet class,
+// G, team, arithmetic (MESS_MODE_*).  Saved by one process (after autotuning) and restored by another
+// (for instance a profiling run, whose own timings would be distorted by the profiler).
+extern "C" mess_status mess_jk_get_tuning(const mess_basis* bc, const mess_jk_opts* opts, int* table, int max_parts,
+                                          int* nparts)
+{
+    if (!bc || !nparts) { mess_set_error("null argument"); return MESS_EINVAL; }
+    mess_basis* b = const_cast<mess_basis*>(bc);
+    mess_jk_opts o{};
+    static double dummy[3];
+    mess_status st = jk_prepare(b, dummy, dummy + 1, dummy + 2, opts, &o);
+    if (st != MESS_OK) return st;
+    const int np = (int)b->bins.parts.size();
+    *nparts = np;
+    if (!table) return MESS_OK;
+    if (max_parts < np) { mess_set_error("mess_jk_get_tuning: %d parts, max_parts = %d", np, max_parts); return MESS_EINVAL; }
+    for (int k = 0; k < np; ++k) {
+        const BinPart& p = b->bins.parts[k];
+        table[4 * k] = p.qclass;
+        table[4 * k + 1] = p.G;
+        table[4 * k + 2] = p.team;
+        table[4 * k + 3] = part_mode(p, o);
+    }
+    return MESS_OK;
+}
+
+extern "C" mess_status mess_jk_set_tuning(const mess_basis* bc, const mess_jk_opts* opts, const int* table, int nparts)
+{
+    if (!bc || !table) { mess_set_error("null argument"); return MESS_EINVAL; }
+    mess_basis* b = const_cast<mess_basis*>(bc);
+    mess_jk_opts o{};
+    static double dummy[3];
+    mess_status st = jk_prepare(b, dummy, dummy + 1, dummy + 2, opts, &o);
+    if (st != MESS_OK) return st;
+    if (nparts != (int)b->bins.parts.size()) {
+        mess_set_error("mess_jk_set_tuning: %d entries for %d parts", nparts, (int)b->bins.parts.size());
+        return MESS_EINVAL;
+    }
+    // validate everything before changing anything
+    for (int k = 0; k < nparts; ++k) {
+        const BinPart& p = b->bins.parts[k];
+        const mess_qclass_info& c = MESS_QCLASS[p.qclass];
+        const int qc = table[4 * k], G = table[4 * k + 1], team = table[4 * k + 2], mode = table[4 * k + 3];
+        bool ok = qc == p.qclass && team >= 0 && team <= 2 && (team == 0 || c.team);
+        ok = ok && (team ? G == 1 : (c.straight ? (G == 1 || G == 4 || G == 8 || G == 32) : G == 1));
+        if (p.fp64) ok = ok && (mode == MESS_MODE_FP64 || (mode == MESS_MODE_DF32 && o.prec == MESS_MIXED && o.split_df32));
+        else ok = ok && mode == (o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);
+        if (!ok) { mess_set_error("mess_jk_set_tuning: entry %d does not fit part %d", k, k); return MESS_EINVAL; }
+    }
+    for (int k = 0; k < nparts; ++k) {
+        BinPart& p = b->bins.parts[k];
+        p.G = table[4 * k + 1];
+        p.team = table[4 * k + 2];
+        p.mode = table[4 * k + 3];
+        p.tuned = 1;
+    }
+    b->bins.generation += 1;
+    mess_free_jk_graphs(b);
+    return MESS_OK;
+}
+
 extern "C" mess_status mess_jk_autotune(const mess_basis* bc, const double* D, const mess_jk_opts* opts, int reps,
                                         int* nchanged)
 {

@@ -196,6 +196,32 @@ def test_jk_autotuned_kernels(mess, oracle_mod, water2_scf, prec, df32):
     assert np.abs(dJ.cpu().numpy() - J).max() < 1e-9
 
 
+def test_jk_tuning_save_restore(mess):
+    """A kernel choice read from one basis restores on another basis of the same molecule, and
+    entries that name a kernel the part does not have are refused without changing anything."""
+    mol = mi.water_cluster(2, 9.0, 11)
+    kw = dict(prec="mixed", split_df32=True)
+    g1 = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
+    g2 = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
+    g1.jk_set_variant(G=32, team=0, split_mode=0, **kw)
+    t1 = g1.jk_tuning(**kw)
+    assert {r[1] for r in t1} <= {1, 32}
+    g2.jk_set_tuning(t1, **kw)
+    assert g2.jk_tuning(**kw) == t1
+    before = g2.jk_tuning(**kw)
+    bad = [list(r) for r in t1]
+    bad[0][1] = 3
+    with pytest.raises(mess.MessError):
+        g2.jk_set_tuning(bad, **kw)
+    with pytest.raises(mess.MessError):
+        g2.jk_set_tuning(t1[:-1], **kw)
+    assert g2.jk_tuning(**kw) == before
+    D = mi.random_symmetric_density(g1.nbf, 5)
+    J1, K1, _ = g1.jk(D, **kw)
+    J2, K2, _ = g2.jk(D, **kw)
+    assert np.abs(J1 - J2).max() < 1e-11 and np.abs(K1 - K2).max() < 1e-11
+
+
 VARIANTS = [(1, 0), (4, 0), (8, 0), (32, 0), (1, 1), (1, 2)]
 
 
