@@ -167,8 +167,12 @@ mess_status mess_schwarz(const mess_basis* b, double* Q);
  * Runs entirely on the GPU: one-electron integrals, Loewdin X (Jacobi eigensolver), the J/K builds of
  * mess_jk_build_device with opts->prec / schwarz_tau / fp64_tau, F = H + J - K/2, DIIS, the
  * diagonalisation of X^T F X (one thread block per molecule, cyclic Jacobi, FP64) and D = 2 C_occ C_occ^T.
+ * With prec MESS_MIXED / MESS_FP32 the iterations use the reduced-precision builds and the reported
+ * energy is that of the final density with one build in which every quartet runs in double-float
+ * (split_df32) or FP64: the integrals' rounding leaves the energy, and the density's residual
+ * error enters it only at second order.
  * D_out (nullable): host n*n final density.  Errors: MESS_ENOCONV (res holds the last iterate),
- * MESS_EINVAL (odd electron count), MESS_ENOTIMPL (n > 256 or a guess other than MESS_GUESS_CORE),
+ * MESS_EINVAL (odd electron count, MESS_GUESS_MLP without weights), MESS_ENOTIMPL (n > 256),
  * MESS_ENOMEM, MESS_ECUDA, MESS_ENUMERIC (singular overlap, non-finite energy). */
 mess_status mess_scf(const mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* D_out);
 
@@ -190,7 +194,8 @@ typedef struct {
     double ms;                   /* launch duration, CUDA events on opts->cuda_stream */
     int G;                       /* lanes per shell quartet (primitive loop split over G lanes) */
     int team;                    /* 1: one warp per shell quartet (level-scheduled recursion), 2: one
-                                    block of 4 warps per quartet, 0: G lanes per quartet */
+                                    block of 4 warps per quartet, 3: one block per quartet whose warps
+                                    split its primitive quartets, 0: G lanes per quartet */
     int mode;                    /* arithmetic: 0 FP64, 1 FP32 + FP64 Boys, 2 FP32, 3 double-float */
 } mess_jk_part;
 
@@ -217,9 +222,10 @@ mess_status mess_profiler_range(int on);
 
 /* Manual kernel choice for the quartet bins of these options (the paper has no counterpart), e.g. to
  * test every kernel variant against the oracle: every part of a straight-line class runs with G lanes
- * per quartet (1, 4, 8 or 32), or one warp (team = 1) or one block of 4 warps (team = 2) per quartet
- * if the class has that kernel; parts of the op-program classes run one warp or block per quartet if
- * team != 0, else one thread per quartet.
+ * per quartet (1, 4, 8 or 32), or one warp (team = 1), one block of 4 warps (team = 2) or one block
+ * whose warps split the primitive quartets (team = 3) per quartet if the class has those kernels;
+ * parts of the op-program classes run one warp or block per quartet if team != 0, else one thread
+ * per quartet.
  * split_mode: -1 keeps the arithmetic of the split parts, 0 = FP64, 3 = double-float (needs
  * prec MESS_MIXED and split_df32).  Kept until the bins are rebuilt for other options or the
  * autotuner runs.  *nchanged (nullable): parts whose kernel changed.  No GPU work.
@@ -230,7 +236,8 @@ mess_status mess_jk_set_variant(const mess_basis* b, const mess_jk_opts* opts, i
 /* Kernel autotuner for the quartet bins of these options (the paper has no counterpart: its kernels
  * come from a tracing compiler).  Each bin part (one shell-quartet class x primitive-count group x
  * precision) can be computed by several kernels: G = 1, 4, 8 or 32 lanes per quartet, one warp per
- * quartet, one block of 4 warps per quartet, and for the split (large-integral) parts FP64 or
+ * quartet, one block of 4 warps per quartet (sharing each recursion level, or splitting the
+ * primitive quartets), and for the split (large-integral) parts FP64 or
  * double-float arithmetic when opts->split_df32 allows it.  Each candidate runs on host density D
  * (nbf x nbf): one untimed launch, then reps timings (clamped to 1..50) of 8 copies launched together
  * on the library's streams, forked from and joined to opts->cuda_stream - the parts of a build run

@@ -580,7 +580,9 @@ template <int TW> __device__ __forceinline__ void team_sync()
     else __syncthreads();
 }
 
-template <typename R, int BMODE, int TW, int L, int NVI, int NH, int NACC, int NVL, int NHL, int NINT,
+// PS (with TW = the block): the block's warps split the quartet's primitive quartets, each warp
+// accumulating into its own copy of the contracted values, summed before the HRR.
+template <typename R, int BMODE, int TW, int PS, int L, int NVI, int NH, int NACC, int NVL, int NHL, int NINT,
           int NA, int NB, int NC, int ND>
 __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable<R>& P, const typename DElem<R>::T* __restrict__ D,
                                              double* __restrict__ J, double* __restrict__ K, int n,
@@ -591,24 +593,29 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
                                              R* __restrict__ sm)
 {
     static_assert(TW == 32 || TW == 32 * MESS_TEAM_WARPS, "a warp or the whole block per quartet");
+    static_assert(!PS || TW == 32 * MESS_TEAM_WARPS, "the primitive split spans the block");
+    constexpr int TP = PS ? 32 : TW;                // threads of one primitive-loop group
     const int slot = threadIdx.x / TW, lane = threadIdx.x % TW;
     const long long q = (long long)blockIdx.x * (32 * MESS_TEAM_WARPS / TW) + slot;
     if (q >= b.total) return;                       // the quartet's threads leave together
+    const int pslot = PS ? (int)(threadIdx.x >> 5) : slot, plane = threadIdx.x % TP;
     R* V = sm + (size_t)slot * (NVI + NH);
     R* H = V + NVI;
+    R* Vp = sm + (size_t)pslot * (NVI + NH);        // the group's own values and contracted sums
+    R* Hp = Vp + NVI;
     const int i = find_bra(b.offs, b.nbra, q);
     const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));
     const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);
-    for (int k = lane; k < NACC; k += TW) H[k] = R(0);
-    team_sync<TW>();
-    const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];
-    const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
+    for (int k = plane; k < NACC; k += TP) Hp[k] = R(0);
+    team_sync<TP>();
+    const int b0 = P.pp_off[bp], nbp = P.pp_n[bp];
+    const int k0 = P.pp_off[kp], nkp = P.pp_n[kp];
     const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);
 #pragma unroll 1
-    for (int ib = b0; ib < b1; ++ib) {
+    for (int ip = PS ? pslot : 0; ip < nbp * nkp; ip += PS ? MESS_TEAM_WARPS : 1) {
+        const int ib = b0 + ip / nkp, ik = k0 + ip % nkp;
         const PrimPair<R> pb = P.load(ib);
-#pragma unroll 1
-        for (int ik = k0; ik < k1; ++ik) {
+        {
             const PrimPair<R> pk = P.load(ik);
             const R rz = R(1) / (pb.zeta + pk.zeta);
             const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;
@@ -625,7 +632,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
             for (int lv = 0; lv < NVL; ++lv) {
                 const int oend = __ldg(vlev + lv + 1);
 #pragma unroll 1
-                for (int o = __ldg(vlev + lv) + lane; o < oend; o += TW) {
+                for (int o = __ldg(vlev + lv) + plane; o < oend; o += TP) {
                     const uint4 w = __ldg(vprog + o);
                     const int kind = w.x & 3, d = (w.x >> 2) & 3;
                     const int m1 = (w.x >> 4) & 15, m2 = (w.x >> 8) & 15, t = w.x >> 16;
@@ -634,23 +641,33 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
                         R f = F[0];
 #pragma unroll
                         for (int m = 1; m <= L; ++m) f = (s1 == m) ? F[m] : f;
-                        V[t] = f;
+                        Vp[t] = f;
                     } else if (kind == 3) {
-                        H[s1] += V[t];
+                        Hp[s1] += Vp[t];
                     } else if (kind == 1) {
-                        R v = pick3(d, pb.PAx, pb.PAy, pb.PAz) * V[s1] + pick3(d, WPx, WPy, WPz) * V[s2];
-                        if (m1) v += small_int<R>(m1) * pb.oo2z * (V[w.z & 0xffff] - roz * V[w.z >> 16]);
-                        V[t] = v;
+                        R v = pick3(d, pb.PAx, pb.PAy, pb.PAz) * Vp[s1] + pick3(d, WPx, WPy, WPz) * Vp[s2];
+                        if (m1) v += small_int<R>(m1) * pb.oo2z * (Vp[w.z & 0xffff] - roz * Vp[w.z >> 16]);
+                        Vp[t] = v;
                     } else {
-                        R v = pick3(d, pk.PAx, pk.PAy, pk.PAz) * V[s1] + pick3(d, WQx, WQy, WQz) * V[s2];
-                        if (m1) v += small_int<R>(m1) * pk.oo2z * (V[w.z & 0xffff] - roe * V[w.z >> 16]);
-                        if (m2) v += small_int<R>(m2) * oo2ze * V[w.w];
-                        V[t] = v;
+                        R v = pick3(d, pk.PAx, pk.PAy, pk.PAz) * Vp[s1] + pick3(d, WQx, WQy, WQz) * Vp[s2];
+                        if (m1) v += small_int<R>(m1) * pk.oo2z * (Vp[w.z & 0xffff] - roe * Vp[w.z >> 16]);
+                        if (m2) v += small_int<R>(m2) * oo2ze * Vp[w.w];
+                        Vp[t] = v;
                     }
                 }
-                team_sync<TW>();
+                team_sync<TP>();
             }
         }
+    }
+    if (PS) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < NACC; k += TW) {
+            R acc = H[k];
+#pragma unroll
+            for (int w = 1; w < MESS_TEAM_WARPS; ++w) acc += sm[(size_t)w * (NVI + NH) + NVI + k];
+            H[k] = acc;
+        }
+        __syncthreads();
     }
     const R ABx = pair_ab(P, bp, 0), ABy = pair_ab(P, bp, 1), ABz = pair_ab(P, bp, 2);
     const R CDx = pair_ab(P, kp, 0), CDy = pair_ab(P, kp, 1), CDz = pair_ab(P, kp, 2);
@@ -732,13 +749,13 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     {                                                                                               \
         return team_smem_bytes<R, __VA_ARGS__>();                                                   \
     }                                                                                               \
-    template <typename R, int BMODE, int TW>                                                        \
+    template <typename R, int BMODE, int TW, int PS>                                                \
     __global__ void __launch_bounds__(32 * MESS_TEAM_WARPS)                                         \
     k_jk_team_##TAG(const BinLaunch b, const PairTable<R> P, const typename DElem<R>::T* __restrict__ D,          \
                     double* __restrict__ J, double* __restrict__ K, int n)                          \
     {                                                                                               \
         extern __shared__ __align__(16) unsigned char mess_team_smem[];                             \
-        jk_team_body<R, BMODE, TW, __VA_ARGS__>(b, P, D, J, K, n, MESS_TEAM_PROG_##TAG,             \
+        jk_team_body<R, BMODE, TW, PS, __VA_ARGS__>(b, P, D, J, K, n, MESS_TEAM_PROG_##TAG,         \
                                             reinterpret_cast<R*>(mess_team_smem));                  \
     }
 #define MESS_DEFINE_TEAM_KERNEL(TAG) MESS_DEFINE_TEAM_KERNEL_IMPL(TAG, MESS_TEAM_ARGS_##TAG)

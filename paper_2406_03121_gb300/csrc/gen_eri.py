@@ -822,30 +822,41 @@ def main(outdir):
               "    } else {",
               ] + ([
               "      if (a.team) {",
-              "        // team 1: a warp per quartet (MESS_TEAM_WARPS per block); team 2: the block on one quartet",
-              "        static int cfg[8][64];   // dynamic shared memory opt-in done, per kernel and device",
-              "        const int qpb = a.team == 2 ? 1 : MESS_TEAM_WARPS;",
+              "        // team 1: a warp per quartet (MESS_TEAM_WARPS per block); 2: the block on one quartet;",
+              "        // 3: the block on one quartet, its warps splitting the primitive quartets",
+              "        static int cfg[12][64];   // dynamic shared memory opt-in done, per kernel and device",
+              "        const int qpb = a.team >= 2 ? 1 : MESS_TEAM_WARPS;",
               "        const long long nbt = (a.bin.total + qpb - 1) / qpb;",
               "        if (nbt > 0x7fffffffLL) return cudaErrorInvalidConfiguration;",
               "        const dim3 gt((unsigned)nbt);",
+              "        if (a.team == 3) {",
+              "            if (a.mode == MESS_MODE_FP64)",
+              f"                return mess_team_launch<double, 0>(k_jk_team_{t}<double, 0, 32 * MESS_TEAM_WARPS, 1>, gt, team_smem_{t}<double>(), a, *a.P64_ptr, cfg[8]);",
+              "            else if (a.mode == MESS_MODE_MIXED)",
+              f"                return mess_team_launch<float, 1>(k_jk_team_{t}<float, 1, 32 * MESS_TEAM_WARPS, 1>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[9]);",
+              "            else if (a.mode == MESS_MODE_DF32)",
+              f"                return mess_team_launch<df32, 3>(k_jk_team_{t}<df32, 3, 32 * MESS_TEAM_WARPS, 1>, gt, team_smem_{t}<df32>(), a, *a.Pdf_ptr, cfg[11]);",
+              "            else",
+              f"                return mess_team_launch<float, 2>(k_jk_team_{t}<float, 2, 32 * MESS_TEAM_WARPS, 1>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[10]);",
+              "        }",
               "        if (a.team == 2) {",
               "            if (a.mode == MESS_MODE_FP64)",
-              f"                return mess_team_launch<double, 0>(k_jk_team_{t}<double, 0, 32 * MESS_TEAM_WARPS>, gt, team_smem_{t}<double>() / MESS_TEAM_WARPS, a, *a.P64_ptr, cfg[4]);",
+              f"                return mess_team_launch<double, 0>(k_jk_team_{t}<double, 0, 32 * MESS_TEAM_WARPS, 0>, gt, team_smem_{t}<double>() / MESS_TEAM_WARPS, a, *a.P64_ptr, cfg[4]);",
               "            else if (a.mode == MESS_MODE_MIXED)",
-              f"                return mess_team_launch<float, 1>(k_jk_team_{t}<float, 1, 32 * MESS_TEAM_WARPS>, gt, team_smem_{t}<float>() / MESS_TEAM_WARPS, a, *a.P32_ptr, cfg[5]);",
+              f"                return mess_team_launch<float, 1>(k_jk_team_{t}<float, 1, 32 * MESS_TEAM_WARPS, 0>, gt, team_smem_{t}<float>() / MESS_TEAM_WARPS, a, *a.P32_ptr, cfg[5]);",
               "            else if (a.mode == MESS_MODE_DF32)",
-              f"                return mess_team_launch<df32, 3>(k_jk_team_{t}<df32, 3, 32 * MESS_TEAM_WARPS>, gt, team_smem_{t}<df32>() / MESS_TEAM_WARPS, a, *a.Pdf_ptr, cfg[7]);",
+              f"                return mess_team_launch<df32, 3>(k_jk_team_{t}<df32, 3, 32 * MESS_TEAM_WARPS, 0>, gt, team_smem_{t}<df32>() / MESS_TEAM_WARPS, a, *a.Pdf_ptr, cfg[7]);",
               "            else",
-              f"                return mess_team_launch<float, 2>(k_jk_team_{t}<float, 2, 32 * MESS_TEAM_WARPS>, gt, team_smem_{t}<float>() / MESS_TEAM_WARPS, a, *a.P32_ptr, cfg[6]);",
+              f"                return mess_team_launch<float, 2>(k_jk_team_{t}<float, 2, 32 * MESS_TEAM_WARPS, 0>, gt, team_smem_{t}<float>() / MESS_TEAM_WARPS, a, *a.P32_ptr, cfg[6]);",
               "        }",
               "        if (a.mode == MESS_MODE_FP64)",
-              f"            return mess_team_launch<double, 0>(k_jk_team_{t}<double, 0, 32>, gt, team_smem_{t}<double>(), a, *a.P64_ptr, cfg[0]);",
+              f"            return mess_team_launch<double, 0>(k_jk_team_{t}<double, 0, 32, 0>, gt, team_smem_{t}<double>(), a, *a.P64_ptr, cfg[0]);",
               "        else if (a.mode == MESS_MODE_MIXED)",
-              f"            return mess_team_launch<float, 1>(k_jk_team_{t}<float, 1, 32>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[1]);",
+              f"            return mess_team_launch<float, 1>(k_jk_team_{t}<float, 1, 32, 0>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[1]);",
               "        else if (a.mode == MESS_MODE_DF32)",
-              f"            return mess_team_launch<df32, 3>(k_jk_team_{t}<df32, 3, 32>, gt, team_smem_{t}<df32>(), a, *a.Pdf_ptr, cfg[3]);",
+              f"            return mess_team_launch<df32, 3>(k_jk_team_{t}<df32, 3, 32, 0>, gt, team_smem_{t}<df32>(), a, *a.Pdf_ptr, cfg[3]);",
               "        else",
-              f"            return mess_team_launch<float, 2>(k_jk_team_{t}<float, 2, 32>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[2]);",
+              f"            return mess_team_launch<float, 2>(k_jk_team_{t}<float, 2, 32, 0>, gt, team_smem_{t}<float>(), a, *a.P32_ptr, cfg[2]);",
               "      }",
               ] if (team_capable(info) or info["mode"] == "program") else []) + ([
               ] + sum([[

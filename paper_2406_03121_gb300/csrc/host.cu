@@ -1021,7 +1021,7 @@ extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, d
 // Autotuner: for every part of the bins, time each kernel variant that computes it (several copies
 // at once, see below) - lanes per
 // quartet G in {1, 4, 8, 32} (straight-line classes), one warp or one block of MESS_TEAM_WARPS warps per
-// quartet (classes with that kernel),
+// quartet, or a block whose warps split the quartet's primitive loop (classes with those kernels),
 // and for the split parts FP64 or double-float arithmetic (when the options allow double-float) -
 // alone on the stream, and keep the fastest.  The choice lives with the bins (a rebuild of the
 // bins for other options starts from the fixed rules again).
@@ -1068,6 +1068,7 @@ static mess_status jk_autotune_device(mess_basis* b, const double* dD, double* d
             if (c.team) {
                 cand.push_back({1, 1, m});
                 cand.push_back({1, 2, m});
+                cand.push_back({1, 3, m});
             }
         }
         const Variant before{p.G, p.team, part_mode(p, o)};
@@ -1143,7 +1144,7 @@ extern "C" mess_status mess_jk_set_variant(const mess_basis* bc, const mess_jk_o
 {
     if (!bc) { mess_set_error("null argument"); return MESS_EINVAL; }
     if (G != 1 && G != 4 && G != 8 && G != 32) { mess_set_error("G must be 1, 4, 8 or 32"); return MESS_EINVAL; }
-    if (team < 0 || team > 2) { mess_set_error("team must be 0, 1 or 2"); return MESS_EINVAL; }
+    if (team < 0 || team > 3) { mess_set_error("team must be 0, 1, 2 or 3"); return MESS_EINVAL; }
     if (split_mode != -1 && split_mode != MESS_MODE_FP64 && split_mode != MESS_MODE_DF32) {
         mess_set_error("split_mode must be -1, 0 (FP64) or 3 (double-float)");
         return MESS_EINVAL;
@@ -1217,7 +1218,7 @@ extern "C" mess_status mess_jk_set_tuning(const mess_basis* bc, const mess_jk_op
         const BinPart& p = b->bins.parts[k];
         const mess_qclass_info& c = MESS_QCLASS[p.qclass];
         const int qc = table[4 * k], G = table[4 * k + 1], team = table[4 * k + 2], mode = table[4 * k + 3];
-        bool ok = qc == p.qclass && team >= 0 && team <= 2 && (team == 0 || c.team);
+        bool ok = qc == p.qclass && team >= 0 && team <= 3 && (team == 0 || c.team);
         ok = ok && (team ? G == 1 : (c.straight ? (G == 1 || G == 4 || G == 8 || G == 32) : G == 1));
         if (p.fp64) ok = ok && (mode == MESS_MODE_FP64 || (mode == MESS_MODE_DF32 && o.prec == MESS_MIXED && o.split_df32));
         else ok = ok && mode == (o.boys_fp64 ? MESS_MODE_MIXED : MESS_MODE_FP32);

@@ -59,7 +59,8 @@ struct BinPart {
     int qclass;
     int fp64;              // 1: evaluated in FP64
     int G;                 // lanes per shell quartet (primitive loop split across G lanes)
-    int team;              // 1: one warp per shell quartet, 2: one block (MESS_TEAM_WARPS warps) per quartet
+    int team;              // 1: one warp per shell quartet, 2: one block (MESS_TEAM_WARPS warps) per quartet,
+                           // 3: one block per quartet whose warps split the primitive quartets
     int mode = -1;         // kernel arithmetic (MESS_MODE_*) chosen by the autotuner; -1: from the options
     int tuned = 0;         // 1: G / team / mode were picked by timing the candidates
     int bra_off, nbra;     // into the concatenated bra / kbeg / offs arrays

@@ -714,6 +714,32 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
             res[m].converged = 0;
         }
     }
+    if (o.prec != MESS_FP64 && !occ_in) {
+        // Reported energy of the reduced-precision forms: E at the final density with one Fock build
+        // in which every quartet runs in FP64-class arithmetic (double-float if split_df32, else
+        // FP64).  The integrals' rounding then no longer enters the energy, and the density's own
+        // deviation from the FP64 solution enters it only at second order (E is stationary there).
+        for (int m = 0; m < b->nmol; ++m) { act[m] = 1; b->active[m] = 1; }
+        b->active_version++;
+        MESS_CUDA_TRY(cudaMemcpyAsync(st.active.p, act.data(), b->nmol, cudaMemcpyHostToDevice, st.s));
+        mess_jk_opts jf = jo;
+        jf.prec = MESS_MIXED;
+        jf.fp64_tau = 1e-300;          // every quartet above the split threshold
+        mess_status js = mess_jk_packed(b, st.D.p, st.Jt.p, st.Kt.p, &jf, nullptr);
+        if (js != MESS_OK) return js;
+        k_axpbypcz<<<eg, 256, 0, st.s>>>(st.F.p, 1.0, st.H.p, 1.0, st.Jt.p, -0.5, st.Kt.p, st.L);
+        k_energy<<<b->nmol, 256, 0, st.s>>>(st.D.p, st.H.p, st.F.p, st.L, st.E.p);
+        MESS_CUDA_TRY(cudaGetLastError());
+        MESS_CUDA_TRY(cudaMemcpyAsync(E.data(), st.E.p, sizeof(double) * b->nmol, cudaMemcpyDeviceToHost, st.s));
+        MESS_CUDA_TRY(cudaStreamSynchronize(st.s));
+        for (int m = 0; m < b->nmol; ++m) {
+            if (!std::isfinite(E[m])) { mess_set_error("molecule %d: non-finite final energy", m); return MESS_ENUMERIC; }
+            if (res) {
+                res[m].E_elec = E[m];
+                res[m].E_total = E[m] + Enuc[m];
+            }
+        }
+    }
     if (status == MESS_ENOCONV) mess_set_error("SCF did not converge within %d iterations", max_iter);
     if (D_out) {
         if (D_out_device) MESS_CUDA_TRY(cudaMemcpyAsync(D_out, st.D.p, sizeof(double) * P, cudaMemcpyDeviceToDevice, st.s));

@@ -190,7 +190,7 @@ def test_jk_autotuned_kernels(mess, oracle_mod, water2_scf, prec, df32):
     parts = g.jk_profile(dD, dJ, dK, **kw)
     assert len(parts) == info["kernel_launches"] - 1 - (prec != "fp64")
     for p in parts:
-        assert p["G"] in (1, 4, 8, 32) and p["team"] in (0, 1, 2)
+        assert p["G"] in (1, 4, 8, 32) and p["team"] in (0, 1, 2, 3)
         assert p["mode"] in ((0, 3) if p["fp64"] and df32 else (0,) if p["fp64"] else (2,))
         assert not (p["team"] and p["G"] != 1)
     assert np.abs(dJ.cpu().numpy() - J).max() < 1e-9
@@ -222,7 +222,7 @@ def test_jk_tuning_save_restore(mess):
     assert np.abs(J1 - J2).max() < 1e-11 and np.abs(K1 - K2).max() < 1e-11
 
 
-VARIANTS = [(1, 0), (4, 0), (8, 0), (32, 0), (1, 1), (1, 2)]
+VARIANTS = [(1, 0), (4, 0), (8, 0), (32, 0), (1, 1), (1, 2), (1, 3)]
 
 
 @pytest.mark.parametrize("G,team", VARIANTS, ids=[f"G{g}_team{t}" for g, t in VARIANTS])
