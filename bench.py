@@ -339,7 +339,7 @@ def run_ours(args):
     tot_flops = sum(p["flops"] for p in prof)
     tot_ms = sum(p["ms"] for p in prof)
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "jk_dram_traffic.json")
+    tfile = os.path.join(ROOT, "profiles", "jk_dram_traffic.txt")
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
