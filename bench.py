@@ -2,6 +2,10 @@
 """Benchmark of the integral-direct, Schwarz-screened J/K build (the hot path of the Hartree-Fock
 energy functional H(P)) on synthetic water clusters.
 
+Also reported (one run each, outside the timed J/K steps): batched SCF molecules/s over seeded alkane
+conformers in the reduced-precision and plain FP64 forms, and the learned SCF guess against the
+core-Hamiltonian and SAD guesses.
+
 One step = one J/K build of the workload's density: every unique shell quartet that passes
 Schwarz screening (tau = 1e-10) is evaluated (Boys, Obara-Saika VRR, contraction, HGP HRR) and
 digested into J and K, then J and K are symmetrised.  Metric: unique Cartesian function quartets
@@ -212,6 +216,42 @@ def _scf_section(mess, args):
     return out
 
 
+def _mlp_section(mess, args):
+    """Learned SCF guess: the MLP trained by the library's own kernels on converged densities of
+    seeded alkane conformers with n = 1..8 (seed 2004), then batched SCF of unseen conformers with
+    n = 9..12 (seed 2005) from the core-Hamiltonian, SAD and learned guesses (reduced precision);
+    iterations to convergence, wall time, and the spread of the final energies across guesses."""
+    import tempfile
+    import mess_inputs as mi
+    sto = mi.basis_path("sto-3g")
+    train = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(args.mlp_molecules, 1, 8, 2004)]
+    test = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(64, 9, 12, 2005)]
+    kw = dict(prec="mixed", split_df32=True)
+    net = mess.MLP(seed=3)
+    t0 = time.perf_counter()
+    losses = net.train(train, epochs=40, batch_rows=4096, lr=2e-3, **kw)
+    t_train = time.perf_counter() - t0
+    out = {"workload": f"train: {len(train)} alkanes n = 1..8 (seed 2004, labels = converged densities of the "
+                       f"library's own SCF); test: {len(test)} alkanes n = 9..12 (seed 2005); STO-3G",
+           "train_seconds": t_train, "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1]}
+    with tempfile.TemporaryDirectory() as d:
+        w = os.path.join(d, "guess.bin")
+        net.save(w)
+        energies = {}
+        for name, guess in (("core", mess.MESS_GUESS_CORE), ("sad", mess.MESS_GUESS_SAD), ("mlp", mess.MESS_GUESS_MLP)):
+            extra = dict(mlp_weights=w) if name == "mlp" else {}
+            mess.scf_batch(test[:2], guess=guess, **kw, **extra)
+            t0 = time.perf_counter()
+            res, st = mess.scf_batch(test, guess=guess, **kw, **extra)
+            dt = time.perf_counter() - t0
+            energies[name] = [r["E_total"] for r in res]
+            out[name] = {"mean_iterations": sum(r["iterations"] for r in res) / len(res),
+                         "converged": sum(int(r["converged"]) for r in res), "molecules_per_s": len(res) / dt}
+    out["max_abs_dE_between_guesses_Ha"] = max(abs(a - b) for k in ("sad", "mlp")
+                                               for a, b in zip(energies[k], energies["core"]))
+    return out
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -372,6 +412,12 @@ def run_ours(args):
     fp64_rate = info64["function_quartets"] * fp64_steps / (ms64 * 1e-3)
 
     scf = _scf_section(mess, args) if args.scf_molecules > 0 else None
+    mlp = None
+    if args.mlp_molecules > 0:
+        try:
+            mlp = _mlp_section(mess, args)
+        except Exception as exc:          # reported in the line; the J/K numbers stand on their own
+            mlp = {"error": f"{type(exc).__name__}: {exc}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -413,6 +459,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu
     if scf:
         line["scf"] = scf
+    if mlp:
+        line["learned_guess"] = mlp
     if args.breakdown:
         line["kernels"] = [{k: p[k] for k in ("la", "lb", "lc", "ld", "fp64", "G", "team", "mode", "shell_quartets",
                                              "primitive_quartets", "flops", "ms")} for p in prof]
@@ -442,6 +490,8 @@ def main():
                     help="write the kernel choice of the timed J/K build to this JSON file")
     ap.add_argument("--scf-molecules", dest="scf_molecules", type=int, default=128,
                     help="alkane conformers of the batched-SCF section (0: skip it)")
+    ap.add_argument("--mlp-molecules", dest="mlp_molecules", type=int, default=512,
+                    help="training conformers of the learned-guess section (0: skip it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -131,7 +131,9 @@ double mess_nuclear_repulsion(const mess_basis* b);
 /* Integral-direct Coulomb and exchange matrices of a symmetric density (Sec. 3 / 5.1 "hfx"):
  * J_mn = sum_ls (mn|ls) D_ls, K_mn = sum_ls (ml|ns) D_ls, over the unique shell quartets that pass
  * Schwarz screening, with the 8-fold permutational symmetry.  D, J, K: host n*n doubles
- * (caller-owned).  opts may be NULL (FP64, no screening).  info may be NULL.
+ * (caller-owned).  opts may be NULL (FP64, no screening).  info may be NULL.  The first call on a
+ * basis allocates a device staging buffer of 3 n^2 doubles kept with the basis (freed by
+ * mess_basis_destroy); the call synchronises opts->cuda_stream before returning.
  * Errors: MESS_EINVAL, MESS_ENOMEM, MESS_ECUDA. */
 mess_status mess_jk_build(const mess_basis* b, const double* D, double* J, double* K,
                           const mess_jk_opts* opts, mess_jk_info* info);

@@ -590,7 +590,7 @@ void mess_free_basis(mess_basis* b)
     for (auto& d : b->d_class_list) d.free();
     b->bins.bra.free(); b->bins.kbeg.free(); b->bins.offs.free();
     mess_free_jk_graphs(b);
-    b->d_D32.free(); b->d_Ddf.free();
+    b->d_D32.free(); b->d_Ddf.free(); b->d_stage.free();
     if (b->dconv_free) cudaEventDestroy(b->dconv_free);
     b->dconv_free = nullptr;
 }
@@ -1260,27 +1260,31 @@ extern "C" mess_status mess_jk_autotune(const mess_basis* bc, const double* D, c
     return MESS_OK;
 }
 
-extern "C" mess_status mess_jk_build(const mess_basis* b, const double* D, double* J, double* K,
+extern "C" mess_status mess_jk_build(const mess_basis* bc, const double* D, double* J, double* K,
                                      const mess_jk_opts* opts, mess_jk_info* info)
 {
-    if (!b || !D || !J || !K) { mess_set_error("null argument"); return MESS_EINVAL; }
+    if (!bc || !D || !J || !K) { mess_set_error("null argument"); return MESS_EINVAL; }
+    mess_basis* b = const_cast<mess_basis*>(bc);
     const size_t nn = (size_t)b->nbf * b->nbf;
-    DevBuf<double> d;
-    MESS_CUDA_TRY(d.alloc(3 * nn));
+    // D, J, K staged in a device buffer kept with the basis (allocated by the first call): repeated
+    // calls allocate nothing, and their builds replay as one CUDA graph
+    if (b->d_stage.n < 3 * nn) MESS_CUDA_TRY(b->d_stage.alloc(3 * nn));
+    double* d = b->d_stage.p;
     mess_jk_opts o{};
     if (opts) o = *opts;
     cudaStream_t s = (cudaStream_t)o.cuda_stream;
     mess_status st = MESS_OK;
-    cudaError_t e = cudaMemcpyAsync(d.p, D, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(d, D, nn * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        st = mess_jk_build_device(b, d.p, d.p + nn, d.p + 2 * nn, &o, info);
+        st = mess_jk_build_device(b, d, d + nn, d + 2 * nn, &o, info);
         if (st == MESS_OK) {
-            e = cudaMemcpyAsync(J, d.p + nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(K, d.p + 2 * nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            e = cudaMemcpyAsync(J, d + nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(K, d + 2 * nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
         }
     }
-    d.free();
+    // the staging buffer is free again only once the stream has drained
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = es;
     if (st != MESS_OK) return st;
     if (e != cudaSuccess) { mess_set_error("jk_build: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
     return MESS_OK;

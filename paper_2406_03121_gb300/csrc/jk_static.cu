@@ -1,6 +1,7 @@
 // mess_jk_build_static: the host-buffer J/K build without any device allocation.
 //
-// mess_jk_build stages D, J and K in device memory it allocates and frees on every call.  Some
+// mess_jk_build stages D, J and K in device memory it allocates (once per basis, with cudaMalloc) and
+// frees when the basis is destroyed.  Some
 // callers cannot let the library allocate: a process whose device memory is owned by its own pool
 // or arena (an inference server, a framework allocator) and must not see cudaMalloc / cudaFree
 // outside it, code on a latency-critical path where cudaFree's implicit device synchronisation is

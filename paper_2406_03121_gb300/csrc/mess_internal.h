@@ -148,6 +148,7 @@ struct mess_basis {
     DevBuf<float2> d_Ddf;
     cudaEvent_t dconv_free = nullptr;
     std::vector<JKGraph> graphs;   // J/K graphs of repeated builds (at most 4, oldest dropped first)
+    DevBuf<double> d_stage;        // D, J, K of the host-buffer J/K build (kept for repeated calls)
 };
 
 // one-electron integrals on the device (one_e.cu)
