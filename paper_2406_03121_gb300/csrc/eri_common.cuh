@@ -369,12 +369,16 @@ __device__ __forceinline__ void jk_add(double* __restrict__ M, size_t idx, R v, 
 // contiguous ket range [kbeg[i], kbeg[i] + offs[i+1] - offs[i]) of the ket list.  A flat quartet
 // index q maps to (i, j) by a binary search over offs.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ int find_bra(const long long* __restrict__ offs, int nbra, long long q)
+// bra of flat quartet q: the largest i with offs[i] <= q, searched between the bras of quartets
+// 32 floor(q / 32) and 32 (floor(q / 32) + 1) (a few steps instead of a search over all bras)
+__device__ __forceinline__ int find_bra(const BinLaunch& b, long long q)
 {
-    int lo = 0, hi = nbra - 1;   // largest i with offs[i] <= q
+    const long long k = q >> 5;
+    int lo = __ldg(b.seg + k);
+    int hi = ((k + 1) << 5) < b.total ? __ldg(b.seg + k + 1) : b.nbra - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(offs + mid) <= q) lo = mid; else hi = mid - 1;
+        if (__ldg(b.offs + mid) <= q) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -399,7 +403,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         const int g = (int)(t0 % G);                                                                \
         const bool valid = q0 < b.total;                                                            \
         const long long q = valid ? q0 : b.total - 1;                                               \
-        const int i = find_bra(b.offs, b.nbra, q);                                                  \
+        const int i = find_bra(b, q);                                                  \
         const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));                            \
         const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);                                     \
         R I[(NA) * (NB) * (NC) * (ND)];                                                             \
@@ -431,7 +435,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
     {                                                                                               \
         const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;                      \
         if (q >= b.total) return;                                                                   \
-        const int i = find_bra(b.offs, b.nbra, q);                                                  \
+        const int i = find_bra(b, q);                                                  \
         const int j = b.kbeg[i] + (int)(q - b.offs[i]);                                             \
         const int bp = b.bra[i], kp = b.ket[j];                                                     \
         double I[(NA) * (NB) * (NC) * (ND)];                                                        \
@@ -603,7 +607,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     R* H = V + NVI;
     R* Vp = sm + (size_t)pslot * (NVI + NH);        // the group's own values and contracted sums
     R* Hp = Vp + NVI;
-    const int i = find_bra(b.offs, b.nbra, q);
+    const int i = find_bra(b, q);
     const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));
     const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);
     for (int k = plane; k < NACC; k += TP) Hp[k] = R(0);

@@ -244,7 +244,19 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
         }
         }
     }
-    if (B.bra.upload(bra) != cudaSuccess || B.kbeg.upload(kbeg) != cudaSuccess || B.offs.upload(offs) != cudaSuccess) {
+    // per part, the bra of every 32nd quartet
+    std::vector<int> seg;
+    for (BinPart& p : B.parts) {
+        p.seg_off = seg.size();
+        const long long* po = offs.data() + p.offs_off;   // [nbra + 1]
+        int i = 0;
+        for (long long q = 0; q < p.total; q += 32) {
+            while (i + 1 < p.nbra && po[i + 1] <= q) ++i;
+            seg.push_back(i);
+        }
+    }
+    if (B.bra.upload(bra) != cudaSuccess || B.kbeg.upload(kbeg) != cudaSuccess || B.offs.upload(offs) != cudaSuccess ||
+        B.seg.upload(seg) != cudaSuccess) {
         mess_set_error("uploading quartet bins failed");
         B.tau = -1.0;
         return MESS_ECUDA;
@@ -313,6 +325,7 @@ static BinLaunch bin_launch(const mess_basis* b, const BinPart& p)
     L.bra = b->bins.bra.p + p.bra_off;
     L.kbeg = b->bins.kbeg.p + p.bra_off;
     L.offs = b->bins.offs.p + p.offs_off;
+    L.seg = b->bins.seg.p + p.seg_off;
     L.ket = b->d_class_list[p.ket_list].p;
     L.nbra = p.nbra;
     L.total = p.total;
@@ -588,7 +601,7 @@ void mess_free_basis(mess_basis* b)
     b->d_pair_mol.free(); b->d_mol_n.free(); b->d_mol_atom_off.free(); b->d_mol_atom_n.free();
     b->d_f_local.free(); b->d_mol_base.free();
     for (auto& d : b->d_class_list) d.free();
-    b->bins.bra.free(); b->bins.kbeg.free(); b->bins.offs.free();
+    b->bins.bra.free(); b->bins.kbeg.free(); b->bins.offs.free(); b->bins.seg.free();
     mess_free_jk_graphs(b);
     b->d_D32.free(); b->d_Ddf.free(); b->d_stage.free();
     if (b->dconv_free) cudaEventDestroy(b->dconv_free);

@@ -26,6 +26,7 @@ struct BinLaunch {
     const int* ket;          // ket list (pair ids, Q descending)
     const long long* offs;   // [nbra + 1] exclusive prefix of ket counts
     const int* kbeg;         // [nbra] first ket index of each bra
+    const int* seg;          // [ceil(total / 32)] bra of quartet 32 k (narrows the bra search)
     int nbra;
     long long total;
 };

@@ -69,6 +69,7 @@ struct BinPart {
     long long fn_quartets; // unique function quartets
     long long prim_quartets;
     size_t offs_off;       // into offs
+    size_t seg_off;        // into seg: bra index of every 32nd quartet of the part
 };
 
 struct BinSet {
@@ -79,6 +80,7 @@ struct BinSet {
     std::vector<BinPart> parts;
     DevBuf<int> bra, kbeg;
     DevBuf<long long> offs;
+    DevBuf<int> seg;
 };
 
 // An instantiated CUDA graph of one J/K build: the bins' generation, the options that select
