@@ -382,10 +382,10 @@ def run_ours(args):
     tfile = os.path.join(ROOT, "profiles", "jk_dram_traffic.txt")
     if os.path.exists(tfile):
         try:
+            # DRAM bytes per launch of a kernel function, from one ncu capture (profiles/*.md)
             tj = json.load(open(tfile))
             key = f"{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']}_{MODE_NAMES[dom['mode']]}_G{dom['G']}_t{dom['team']}"
-            if tj.get("workload") == args.workload and key in tj.get("kernels", {}):
-                traffic = tj["kernels"][key]
+            traffic = tj.get(args.workload, {}).get(key)
         except Exception:
             traffic = None
 
