@@ -54,6 +54,20 @@ def _build_library():
     ge.build()
 
 
+def max_over_ranks(dist, value, device):
+    """The largest of every rank's value (the slowest replica sets the job's time); dist may be None."""
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_step, steps, max_ms):
+    """Units processed by all ranks (each runs its own replica of the workload) per second."""
+    return world * units_per_step * steps / (max_ms * 1e-3)
+
+
 def _workload(name):
     import mess_inputs as mi
     w = WORKLOADS[name]
@@ -341,12 +355,9 @@ def run_ours(args):
     if dist:
         dist.barrier(device_ids=[local_rank])
     clk = clocks.stop()
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = max_over_ranks(dist, total_ms, dev)
     fnq = info["function_quartets"]
-    value = world * fnq * args.steps / (max_ms * 1e-3)
+    value = whole_job_rate(world, fnq, args.steps, max_ms)
     J_mix, K_mix = dJ.cpu().numpy(), dK.cpu().numpy()
 
     # roofline of the dominant kernel: per-launch CUDA events on the launching stream
