@@ -401,10 +401,14 @@ def run_ours(args):
             traffic = None
 
     # end to end through the public host-buffer call: H2D of D, the build, D2H of J and K
+    # (D, J and K in page-locked host memory: the copies run at full link speed)
+    D_pin = torch.from_numpy(D).pin_memory()
+    J_pin, K_pin = torch.empty_like(D_pin).pin_memory(), torch.empty_like(D_pin).pin_memory()
+    D_h, J_h, K_h = D_pin.numpy(), J_pin.numpy(), K_pin.numpy()
     e2e_t = []
     for _ in range(max(2, min(args.steps, 5))):
         t0 = time.perf_counter()
-        g.jk(D, **tune_kw)
+        g.jk(D_h, J=J_h, K=K_h, **tune_kw)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_t)
 
@@ -463,7 +467,8 @@ def run_ours(args):
                      "peak_source": f"measured FMA-chain peak of this GPU ({'FP64' if dom_fp64_pipe else 'FP32'})",
                      "whole_build": {"achieved": tot_flops / (tot_ms * 1e-3) / 1e12, "ms": tot_ms}},
         "peaks_measured_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
-        "e2e": {"value": fnq / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8},
+        "e2e": {"value": fnq / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8,
+                "call": "mess_jk_build on page-locked host D, J, K (copies and synchronisation inside the timing)"},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }
     if cpu:

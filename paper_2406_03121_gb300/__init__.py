@@ -261,10 +261,15 @@ class Basis:
         _check(mess_eri_tensor(self._h, _dptr(out)), "mess_eri_tensor")
         return out
 
-    def jk(self, D, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, boys_fp64=False, split_df32=False):
-        """J, K of a host density (numpy); returns (J, K, info dict)."""
+    def jk(self, D, prec="fp64", schwarz_tau=0.0, fp64_tau=0.0, boys_fp64=False, split_df32=False, J=None, K=None):
+        """J, K of a host density (numpy); returns (J, K, info dict).  J, K (optional): caller-owned
+        C-contiguous float64 n x n outputs, e.g. views of page-locked host memory."""
         D = np.ascontiguousarray(D, dtype=np.float64)
-        J, K = np.zeros_like(D), np.zeros_like(D)
+        for X in (J, K):
+            if X is not None and (X.dtype != np.float64 or X.shape != D.shape or not X.flags.c_contiguous):
+                raise ValueError("J and K must be C-contiguous float64 arrays shaped like D")
+        J = np.zeros_like(D) if J is None else J
+        K = np.zeros_like(D) if K is None else K
         info = mess_jk_info()
         o = jk_opts(prec, schwarz_tau, fp64_tau, None, boys_fp64, split_df32)
         _check(mess_jk_build(self._h, _dptr(D), _dptr(J), _dptr(K), ctypes.byref(o), ctypes.byref(info)),
