@@ -1,0 +1,191 @@
+"""The recursion programs the kernel generator emits, checked on the CPU against the oracle.
+
+For every shell-quartet class, the Obara-Saika VRR + Head-Gordon-Pople HRR op programs (the
+one-thread-per-quartet form and the level-scheduled form of the warp/block-per-quartet kernels)
+are interpreted exactly as the kernels decode them, on one primitive quartet with random
+exponents and centres and unit coefficients, and the resulting raw integrals are compared with
+the oracle's (a different exact route, McMurchie-Davidson) for the same raw primitives.  The
+level-scheduled programs are also checked for what lane-parallel execution needs: within one
+level, no op reads a slot that another op of the level writes, and no two ops write one slot.
+"""
+import importlib.util
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _gen():
+    path = os.path.join(ROOT, "paper_2406_03121_gb300", "csrc", "gen_eri.py")
+    spec = importlib.util.spec_from_file_location("gen_eri_under_test", path)
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+GEN = _gen()
+CLASSES = GEN.QUARTET_CLASSES
+
+
+def _pair(a, A, b, B):
+    """Gaussian product of two unit-coefficient primitives, as the pair records hold it."""
+    z = a + b
+    P = (a * A + b * B) / z
+    K = math.sqrt(2.0) * math.pi ** 1.25 * math.exp(-a * b / z * float(np.dot(A - B, A - B))) / z
+    return dict(z=z, P=P, PA=P - A, K=K, oo2z=0.5 / z, AB=A - B)
+
+
+def _vrr_inputs(pb, pk, L):
+    rz = 1.0 / (pb["z"] + pk["z"])
+    roz, roe = pk["z"] * rz, pb["z"] * rz
+    PQ = pb["P"] - pk["P"]
+    T = pb["z"] * roz * float(np.dot(PQ, PQ))
+    F = oracle.boys(L, T) * pb["K"] * pk["K"] * math.sqrt(rz)
+    return dict(F=F, roz=roz, roe=roe, oo2ze=0.5 * rz, WP=-roz * PQ, WQ=roe * PQ)
+
+
+def _vrr_op(op, Vr, Vw, H, pb, pk, x):
+    """One VRR op, decoded as the kernels decode it: reads Vr, writes Vw (or accumulates into H).
+    Returns (V slots read, slot written, "V" or "H")."""
+    kind, t, s1, s2, s3, s4, s5, d, m1, m2 = op
+    if kind == 0:
+        Vw[t] = x["F"][s1]
+        return [], t, "V"
+    if kind == 3:
+        H[s1] += Vr[t]
+        return [t], s1, "H"
+    if kind == 1:
+        v = pb["PA"][d] * Vr[s1] + x["WP"][d] * Vr[s2]
+        reads = [s1, s2]
+        if m1:
+            v += m1 * pb["oo2z"] * (Vr[s3] - x["roz"] * Vr[s4])
+            reads += [s3, s4]
+    else:
+        v = pk["PA"][d] * Vr[s1] + x["WQ"][d] * Vr[s2]
+        reads = [s1, s2]
+        if m1:
+            v += m1 * pk["oo2z"] * (Vr[s3] - x["roe"] * Vr[s4])
+            reads += [s3, s4]
+        if m2:
+            v += m2 * x["oo2ze"] * Vr[s5]
+            reads += [s5]
+    Vw[t] = v
+    return reads, t, "V"
+
+
+def _hrr_op(op, Hr, Hw, AB, CD):
+    t, s1, s2, d, side = op
+    Hw[t] = Hr[s1] + (CD if side else AB)[d] * Hr[s2]
+    return [s1, s2], t
+
+
+def _run(prog, team, pb, pk, L):
+    x = _vrr_inputs(pb, pk, L)
+    V = np.full(max(prog["nv"], 1), np.nan)
+    H = np.zeros(max(prog["nh"], prog["nacc"], 1))
+    H[prog["nacc"]:] = np.nan
+    if team:
+        # lane-parallel levels: every op of a level sees the values from before the level
+        lv = prog["vlev"]
+        for k in range(len(lv) - 1):
+            Vb = V.copy()
+            vreads, vwrites, hwrites = set(), [], []
+            for op in prog["vrr"][lv[k]:lv[k + 1]]:
+                reads, w, arr = _vrr_op(op, Vb, V, H, pb, pk, x)
+                vreads.update(reads)
+                (vwrites if arr == "V" else hwrites).append(w)
+            assert len(set(vwrites)) == len(vwrites), "two VRR ops of one level write the same slot"
+            assert len(set(hwrites)) == len(hwrites), "two accumulations of one level hit the same slot"
+            assert not (vreads & set(vwrites)), "an op reads a slot written in its own level"
+        hl = prog["hlev"]
+        for k in range(len(hl) - 1):
+            Hb = H.copy()
+            reads_all, writes = set(), []
+            for op in prog["hrr"][hl[k]:hl[k + 1]]:
+                reads, w = _hrr_op(op, Hb, H, pb["AB"], pk["AB"])
+                writes.append(w)
+                reads_all.update(reads)
+            assert len(set(writes)) == len(writes), "two HRR ops of one level write the same slot"
+            assert not (reads_all & set(writes)), "an HRR op reads a slot written in its own level"
+    else:
+        for op in prog["vrr"]:
+            _vrr_op(op, V, V, H, pb, pk, x)
+        for op in prog["hrr"]:
+            _hrr_op(op, H, H, pb["AB"], pk["AB"])
+    out = np.array([H[s] for s, _ in prog["fin"]])
+    assert np.all(np.isfinite(out)), "a final integral reads a slot never written"
+    return out
+
+
+def _oracle_raw(cls, exps, centres):
+    """Raw-primitive integrals (unit coefficients, no normalisation) in the kernels' index order."""
+    (la, lb), (lc, ld) = cls
+    ls = [la, lb, lc, ld]
+    center, lmn, first = [], [], []
+    for l, R in zip(ls, centres):
+        first.append(len(lmn))
+        for comp in GEN.cart(l):
+            center.append(R)
+            lmn.append(comp)
+    n = len(lmn)
+    nprim = np.ones(n, dtype=np.int32)
+    poff = np.arange(n, dtype=np.int32)
+    ex = np.array([exps[s] for s in range(4) for _ in GEN.cart(ls[s])], dtype=np.float64)
+    b = oracle.Basis(n, np.ascontiguousarray(np.array(center, dtype=np.float64)),
+                     np.ascontiguousarray(np.array(lmn, dtype=np.int32)), nprim, poff, ex,
+                     np.ones(n), np.arange(n, dtype=np.int32), n, np.zeros(n, dtype=np.int32),
+                     np.zeros(1, dtype=np.int32), np.zeros((1, 3)))
+    out = []
+    for i in range(GEN.ncart(la)):
+        for j in range(GEN.ncart(lb)):
+            for k in range(GEN.ncart(lc)):
+                for m in range(GEN.ncart(ld)):
+                    out.append(oracle.eri(b, first[0] + i, first[1] + j, first[2] + k, first[3] + m))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("cls", CLASSES, ids=[GEN.tag(c) for c in CLASSES])
+def test_programs_match_oracle(cls):
+    (la, lb), (lc, ld) = cls
+    rng = np.random.default_rng(100 + 7 * la + 5 * lb + 3 * lc + ld)
+    L = la + lb + lc + ld
+    for trial in range(2):
+        exps = rng.uniform(0.3, 2.5, 4)
+        centres = [rng.normal(scale=0.8, size=3) for _ in range(4)]
+        if trial == 1:
+            centres[1] = centres[0].copy()        # one-centre bra pair (AB = 0)
+        pb = _pair(exps[0], centres[0], exps[1], centres[1])
+        pk = _pair(exps[2], centres[2], exps[3], centres[3])
+        ref = _oracle_raw(cls, exps, centres)
+        scale = np.abs(ref).max()
+        team = GEN.build_team_program(cls)
+        got = _run(team, True, pb, pk, L)
+        assert np.abs(got - ref).max() <= 1e-11 * scale + 1e-14, "level-scheduled program"
+        prog = GEN.build_program(cls)
+        got = _run(prog, False, pb, pk, L)
+        assert np.abs(got - ref).max() <= 1e-11 * scale + 1e-14, "op program"
+
+
+@pytest.mark.parametrize("cls", CLASSES, ids=[GEN.tag(c) for c in CLASSES])
+def test_component_scales(cls):
+    """The per-integral scale of the final values is the product of the four components' factors
+    sqrt((2L-1)!! / ((2l-1)!! (2m-1)!! (2n-1)!!)), which turns the x^L-normalised shell into unit
+    norm for every component (1 for s and p, sqrt(3) off-diagonal for d: xy, xz, yz)."""
+    (la, lb), (lc, ld) = cls
+    prog = GEN.build_team_program(cls)
+    d = {(2, 0, 0): 1.0, (0, 2, 0): 1.0, (0, 0, 2): 1.0, (1, 1, 0): math.sqrt(3.0), (1, 0, 1): math.sqrt(3.0),
+         (0, 1, 1): math.sqrt(3.0)}
+    fac = lambda l, c: d[c] if l == 2 else 1.0  # noqa: E731
+    k = 0
+    for a in GEN.cart(la):
+        for b in GEN.cart(lb):
+            for c in GEN.cart(lc):
+                for e in GEN.cart(ld):
+                    want = fac(la, a) * fac(lb, b) * fac(lc, c) * fac(ld, e)
+                    assert prog["fin"][k][1] == pytest.approx(want, rel=1e-15)
+                    k += 1
