@@ -217,6 +217,12 @@ mess_status mess_jk_profile(const mess_basis* b, const double* dD, double* dJ, d
 mess_status mess_jk_get_tuning(const mess_basis* b, const mess_jk_opts* opts, int* table, int max_parts, int* nparts);
 mess_status mess_jk_set_tuning(const mess_basis* b, const mess_jk_opts* opts, const int* table, int nparts);
 
+/* Diagnostic: the Boys-function grid the J/K kernels expand around (Sec. 3's closed-form integrals
+ * need F_m(T)): row k holds F_0..F_15(T_k) and exp(-T_k) at T_k = k * *dT (0.1).  Host-only, no GPU.
+ * *nrows, *ncols, *dT (each nullable) receive the shape and spacing; out (nullable) receives
+ * nrows * ncols doubles row-major if max_values suffices, else MESS_EINVAL. */
+mess_status mess_boys_grid(double* out, int max_values, int* nrows, int* ncols, double* dT);
+
 /* Diagnostic (not part of the paper's method): marks the start (on != 0) or end of the region a
  * kernel profiler started with profiling off at launch (ncu --profile-from-start off) records, so
  * that set-up work (autotuning, warm-up) stays out of a capture.  Errors: MESS_ECUDA. */

@@ -30,7 +30,7 @@ EXPORTED = [
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
     "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
     "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_jk_autotune", "mess_jk_set_variant",
-    "mess_jk_get_tuning", "mess_jk_set_tuning", "mess_profiler_range", "mess_fma_peak",
+    "mess_jk_get_tuning", "mess_jk_set_tuning", "mess_boys_grid", "mess_profiler_range", "mess_fma_peak",
     "mess_last_error",
     "mess_mlp_num_params", "mess_mlp_create", "mess_mlp_destroy", "mess_mlp_get_params", "mess_mlp_set_params",
     "mess_mlp_save", "mess_mlp_load", "mess_mlp_features", "mess_mlp_loss_grad", "mess_mlp_train",
@@ -126,6 +126,7 @@ mess_jk_set_variant = _sig("mess_jk_set_variant", ctypes.c_int,
 mess_jk_get_tuning = _sig("mess_jk_get_tuning", ctypes.c_int,
                           [_P, ctypes.POINTER(mess_jk_opts), _IP, ctypes.c_int, _IP])
 mess_jk_set_tuning = _sig("mess_jk_set_tuning", ctypes.c_int, [_P, ctypes.POINTER(mess_jk_opts), _IP, ctypes.c_int])
+mess_boys_grid = _sig("mess_boys_grid", ctypes.c_int, [_DP, ctypes.c_int, _IP, _IP, _DP])
 mess_profiler_range = _sig("mess_profiler_range", ctypes.c_int, [ctypes.c_int])
 mess_fma_peak = _sig("mess_fma_peak", ctypes.c_int, [_DP, _DP, _P])
 mess_last_error = _sig("mess_last_error", ctypes.c_char_p, [])
@@ -344,6 +345,15 @@ class Basis:
         out["status"] = st
         out["D"] = D
         return out
+
+
+def boys_grid():
+    """The kernels' Boys-function grid: (table [rows, 17] = F_0..F_15 and exp(-T) per row, dT)."""
+    nr, nc, dT = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(mess_boys_grid(None, 0, ctypes.byref(nr), ctypes.byref(nc), ctypes.byref(dT)), "mess_boys_grid")
+    t = np.zeros((nr.value, nc.value))
+    _check(mess_boys_grid(_dptr(t), t.size, None, None, None), "mess_boys_grid")
+    return t, dT.value
 
 
 def profiler_range(on):

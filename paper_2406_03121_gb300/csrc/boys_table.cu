@@ -29,3 +29,19 @@ void mess_boys_table(std::vector<double>& tab)
         tab[(size_t)k * MESS_BOYS_NCOL + MESS_BOYS_NF] = (double)eT;
     }
 }
+
+extern "C" mess_status mess_boys_grid(double* out, int max_values, int* nrows, int* ncols, double* dT)
+{
+    if (nrows) *nrows = MESS_BOYS_NROW;
+    if (ncols) *ncols = MESS_BOYS_NCOL;
+    if (dT) *dT = MESS_BOYS_DT;
+    if (!out) return MESS_OK;
+    if (max_values < MESS_BOYS_NROW * MESS_BOYS_NCOL) {
+        mess_set_error("mess_boys_grid: %d values needed, max_values = %d", MESS_BOYS_NROW * MESS_BOYS_NCOL, max_values);
+        return MESS_EINVAL;
+    }
+    std::vector<double> tab;
+    mess_boys_table(tab);
+    for (size_t i = 0; i < tab.size(); ++i) out[i] = tab[i];
+    return MESS_OK;
+}
