@@ -262,8 +262,8 @@ mess_status mess_jk_autotune(const mess_basis* b, const double* D, const mess_jk
 mess_status mess_fma_peak(double* fp32_tflops, double* fp64_tflops, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------------------
- * Learned initial density (spec extension; the paper motivates combining ML models with the
- * SCF, Sec. 1 and its use of Adam, Sec. 5).  A multilayer perceptron 112 -> 256 -> 256 -> 25 (SiLU)
+ * Learned initial density (an addition to the paper's method; the paper motivates combining ML
+ * models with the SCF, Sec. 1, and uses Adam, Sec. 5).  A multilayer perceptron 112 -> 256 -> 256 -> 25 (SiLU)
  * maps descriptors of an ordered atom pair (element one-hots, a Gaussian radial basis of the pair
  * distance, radial environments of both atoms) to the 5 x 5 density block of the pair in a frame
  * with z along the pair axis (minimal basis: 1 function on H, s s' p on C / N / O, e.g. STO-3G).
