@@ -15,6 +15,7 @@
 #include <vector>
 
 #include <cuda_profiler_api.h>
+#include <cstdlib>
 
 #include "mess_internal.h"
 
@@ -287,12 +288,16 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
 // Per-device pool of non-blocking streams: the class launches of one J/K build fork from the
 // caller's stream, run concurrently (most of them are small), and join back before the
 // symmetrisation.  Fork/join is by events, so a captured caller stream captures the whole build.
-#define MESS_NSTREAMS 16
+// The number of streams is MESS_JK_STREAMS from the environment when the pool is created (8..64),
+// else 16.
+#define MESS_MAX_STREAMS 64
+#define MESS_DEFAULT_STREAMS 16
 #define MESS_TUNE_COPIES 8   // concurrent copies of a candidate kernel timed by the autotuner
 struct StreamPool {
     bool init = false;
-    cudaStream_t s[MESS_NSTREAMS];
-    cudaEvent_t fork, join[MESS_NSTREAMS];
+    int n = MESS_DEFAULT_STREAMS;
+    cudaStream_t s[MESS_MAX_STREAMS];
+    cudaEvent_t fork, join[MESS_MAX_STREAMS];
     cudaStream_t capture;   // private stream on which J/K graphs are captured
     std::mutex mu;
 };
@@ -307,7 +312,10 @@ static cudaError_t get_pool(StreamPool** out)
     StreamPool& P = g_pools[dev];
     std::lock_guard<std::mutex> lk(P.mu);
     if (!P.init) {
-        for (int i = 0; i < MESS_NSTREAMS; ++i) {
+        const char* env = getenv("MESS_JK_STREAMS");
+        int n = env ? atoi(env) : MESS_DEFAULT_STREAMS;
+        P.n = std::max(MESS_TUNE_COPIES, std::min(MESS_MAX_STREAMS, n));
+        for (int i = 0; i < P.n; ++i) {
             if ((e = cudaStreamCreateWithFlags(&P.s[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
             if ((e = cudaEventCreateWithFlags(&P.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
         }
@@ -799,7 +807,7 @@ static mess_status jk_enqueue(mess_basis* b, const mess_jk_opts& o, const double
     const bool concurrent = pool != nullptr;
     if (concurrent) {
         MESS_CUDA_TRY(cudaEventRecord(pool->fork, s));
-        for (int i = 0; i < MESS_NSTREAMS; ++i) MESS_CUDA_TRY(cudaStreamWaitEvent(pool->s[i], pool->fork, 0));
+        for (int i = 0; i < pool->n; ++i) MESS_CUDA_TRY(cudaStreamWaitEvent(pool->s[i], pool->fork, 0));
     }
     mess_status out = MESS_OK;
     for (size_t r = 0; r < order.size(); ++r) {
@@ -820,7 +828,7 @@ static mess_status jk_enqueue(mess_basis* b, const mess_jk_opts& o, const double
         a.J = dJ;
         a.K = dK;
         a.n = b->nbf;
-        a.stream = concurrent ? pool->s[r % MESS_NSTREAMS] : s;
+        a.stream = concurrent ? pool->s[r % pool->n] : s;
         if (ev) cudaEventRecord((*ev)[2 * k], s);
         cudaError_t e = MESS_CLASS_LAUNCHERS[p.qclass](a);
         if (ev) cudaEventRecord((*ev)[2 * k + 1], s);
@@ -837,7 +845,7 @@ static mess_status jk_enqueue(mess_basis* b, const mess_jk_opts& o, const double
     }
     if (concurrent) {
         // join: s waits for every pool stream (also after a failed launch)
-        for (int i = 0; i < MESS_NSTREAMS; ++i) {
+        for (int i = 0; i < pool->n; ++i) {
             cudaEventRecord(pool->join[i], pool->s[i]);
             cudaStreamWaitEvent(s, pool->join[i], 0);
         }
