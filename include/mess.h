@@ -22,7 +22,10 @@
  *     returns a message for the calling thread's most recent failure.
  *   - Threads: calls on distinct bases are independent.  A mess_basis may be shared by calls that do
  *     not overlap in time on the host (it caches screening bins); device-pointer calls on the same
- *     basis may overlap on the GPU.
+ *     basis may overlap on the GPU (their builds take turns with the basis's reduced-precision
+ *     density copies).
+ *   - Environment: MESS_JK_STREAMS (8..64, default 16), read once per device, sets how many
+ *     streams the parts of one J/K build are spread over.
  */
 #ifndef MESS_H
 #define MESS_H
