@@ -12,7 +12,7 @@ digested into J and K, then J and K are symmetrised.  Metric: unique Cartesian f
 per second (after screening) in the reduced-precision mode, whose energy error against the FP64
 path is reported beside it (bar: <= 1e-6 Ha); the plain FP64 path is timed on the same input.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload water8]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload water32|water8]
 
 N > 1 runs under torchrun: independent replicas of the workload, one per GPU (weak scaling).
 """
@@ -179,23 +179,100 @@ def _nvsmi_index(torch, local_rank):
         return local_rank
 
 
-def _oracle_rate(mol, basis_path, nelem, seed=7):
-    """The FP64 CPU oracle as it stands: nelem sampled J/K elements of the workload by their
-    defining sums over all (l, s) (every integral evaluated, no screening); returns (integral
-    evaluations per second, threads, seconds)."""
+def _oracle_counts(o, Q, rows, cols, tau):
+    """Integrals the oracle's defining sums evaluate for the elements (rows, cols): for J_mn every
+    (l, s) with Q_mn Q_ls >= tau, for K_mn every (l, s) with Q_ml Q_ns >= tau (the screening rule of
+    both sides; Q per function from its shell's Schwarz factor)."""
+    import numpy as np
+    sh = np.asarray(o.shell)
+    Qf = np.asarray(Q)[np.ix_(sh, sh)]
+    total = 0
+    for m, a in zip(rows, cols):
+        if tau <= 0.0:
+            total += 2 * o.nfn * o.nfn
+            continue
+        total += int(np.count_nonzero(Qf[m, a] * Qf >= tau))
+        total += int(np.count_nonzero(np.multiply.outer(Qf[m, :], Qf[a, :]) >= tau))
+    return total
+
+
+def _oracle_rate(mol, basis_path, D, nelem, seed=7, tau=SCHWARZ_TAU):
+    """The FP64 CPU oracle as it stands on a bounded sample of the workload: nelem seeded J/K
+    elements of the workload's density, each by its defining sum over all (l, s) with the same
+    Schwarz screening as the GPU build.  Each evaluation is one function-quartet integral (the
+    oracle's unit of work in its full symmetric build as well).  Returns (evaluations per second,
+    threads, seconds, evaluations)."""
     import numpy as np
     import oracle
     oracle.build()
     o = oracle.basis_for(mol, basis_path)
+    Q = oracle.schwarz(o)
     rng = np.random.default_rng(seed)
     rows = rng.integers(0, o.nfn, nelem)
     cols = rng.integers(0, o.nfn, nelem)
-    D = np.eye(o.nfn)
     t0 = time.perf_counter()
-    oracle.jk_elements(o, D, rows, cols)
+    oracle.jk_elements(o, D, rows, cols, tau=tau, Q=Q)
     dt = time.perf_counter() - t0
-    evals = 2 * nelem * o.nfn * o.nfn       # one integral per (l, s) for J and for K
-    return evals / dt, oracle.num_threads(), dt
+    evals = _oracle_counts(o, Q, rows, cols, tau)
+    return evals / dt, oracle.num_threads(), dt, evals
+
+
+def _oracle_full_h2o():
+    """The oracle's full J/K build of one water in STO-3G (7 functions, 406 unique function quartets,
+    its symmetric loop) on a seeded density, with one thread and with every processor: seconds and
+    unique function quartets per second (best of 20 calls each)."""
+    import mess_inputs as mi
+    import oracle
+    oracle.build()
+    o = oracle.basis_for(mi.h2o(), mi.basis_path("sto-3g"))
+    D = mi.random_symmetric_density(o.nfn, 1)
+    nq = (o.nfn * (o.nfn + 1) // 2) * (o.nfn * (o.nfn + 1) // 2 + 1) // 2
+    out = {"workload": "H2O / STO-3G (7 functions), full J/K by the oracle's 8-fold symmetric loop",
+           "unique_function_quartets": nq}
+    for name, threads in (("one_thread", 1), ("all_threads", 0)):
+        oracle.set_num_threads(threads)
+        best = 1e30
+        for _ in range(20):
+            t0 = time.perf_counter()
+            oracle.jk(o, D)
+            best = min(best, time.perf_counter() - t0)
+        out[name] = {"threads": oracle.num_threads(), "seconds": best, "unique_function_quartets_per_s": nq / best}
+    oracle.set_num_threads(0)
+    return out
+
+
+def _source_digest():
+    """Digest of the library's kernel and host sources (the counters of a profile taken with other
+    sources no longer describe these kernels)."""
+    import hashlib
+    h = hashlib.sha256()
+    pkg = os.path.join(ROOT, "paper_2406_03121_gb300")
+    for d in (os.path.join(pkg, "csrc"), os.path.join(ROOT, "include")):
+        for f in sorted(os.listdir(d)):
+            if f.endswith((".cu", ".cuh", ".h", ".py")):
+                h.update(f.encode())
+                with open(os.path.join(d, f), "rb") as fh:
+                    h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload, key, launches):
+    """DRAM bytes per launch of a kernel function of the build, from the ncu capture summarised in
+    profiles/jk_dram_traffic.txt, if that capture was taken with the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "jk_dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    try:
+        body = "".join(line for line in open(path) if not line.lstrip().startswith("#"))
+        tj = json.loads(body)
+    except Exception:
+        return None
+    if tj.get("source_digest") != _source_digest():
+        return None
+    rec = tj.get("workloads", {}).get(workload, {}).get(key)
+    if not rec or rec.get("launches") != launches:
+        return None
+    return rec["dram_bytes_total"] / rec["launches"]
 
 
 def _kernel_label(p):
@@ -222,10 +299,14 @@ def _scf_section(mess, args):
         res, st = mess.scf_batch(bases, **kw)
         dt = time.perf_counter() - t0
         energies[name] = [r["E_total"] for r in res]
+        energies[name + "_iter"] = [r["E_iter"] for r in res]
         out[name] = {"molecules_per_s": len(bases) / dt, "seconds": dt,
                      "converged": sum(int(r["converged"]) for r in res),
                      "mean_iterations": sum(r["iterations"] for r in res) / len(res)}
     out["max_abs_dE_mixed_vs_fp64_Ha"] = max(abs(a - b) for a, b in zip(energies["mixed"], energies["fp64"]))
+    # the reduced-precision iterations' own energy (before the final full-precision evaluation)
+    out["max_abs_dE_mixed_iterations_vs_fp64_Ha"] = max(abs(a - b) for a, b in
+                                                         zip(energies["mixed_iter"], energies["fp64"]))
     out["speedup_of_reduced_precision"] = out["mixed"]["molecules_per_s"] / out["fp64"]["molecules_per_s"]
     return out
 
@@ -267,29 +348,42 @@ def _mlp_section(mess, args):
 
 
 def run_reference(args):
+    """The oracle as it stands, on the host cores, over the same workload: each step one bounded
+    sample of it (per_step seeded J/K elements of the workload's converged-density stand-in, each by
+    its screened defining sum).  Rate = function-quartet integrals evaluated per second."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
+    import mess_inputs as mi
     mol, bpath, w = _workload(args.workload)
-    per_step = 16
+    per_step = 8
+    import oracle
+    oracle.build()
+    nfn = oracle.basis_for(mol, bpath).nfn
+    D = mi.random_symmetric_density(nfn, w["seed"], nocc=sum(int(z) for z in mol.Z) // 2)
     for _ in range(args.warmup):
-        _oracle_rate(mol, bpath, per_step)
-    rates, total = [], 0.0
+        _oracle_rate(mol, bpath, D, 1)
+    rates, total, evals = [], 0.0, 0
+    threads = 0
     for k in range(args.steps):
-        r, threads, dt = _oracle_rate(mol, bpath, per_step, seed=100 + k)
+        r, threads, dt, ev = _oracle_rate(mol, bpath, D, per_step, seed=100 + k)
         rates.append(r)
         total += dt
-    value = sum(rates) / len(rates)
+        evals += ev
+    value = evals / total
+    unit = "function-quartet integrals/s"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": w["desc"], "schwarz_tau": SCHWARZ_TAU,
                    "l2": "host CPU run"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{per_step} sampled J/K elements per step, each by its defining sum over "
-                                   f"all (l, s) (2 n^2 integral evaluations per element, one function quartet each)"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} seeded J/K elements per step, each by its defining sum over all "
+                                   f"(l, s) with the same Schwarz screening (tau = {SCHWARZ_TAU:g}); every "
+                                   f"evaluation is one function-quartet integral, the unit of work of the "
+                                   f"GPU metric's unique function quartets"},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -389,16 +483,8 @@ def run_ours(args):
     achieved = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
     tot_flops = sum(p["flops"] for p in prof)
     tot_ms = sum(p["ms"] for p in prof)
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "jk_dram_traffic.txt")
-    if os.path.exists(tfile):
-        try:
-            # DRAM bytes per launch of a kernel function, from one ncu capture (profiles/*.md)
-            tj = json.load(open(tfile))
-            key = f"{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']}_{MODE_NAMES[dom['mode']]}_G{dom['G']}_t{dom['team']}"
-            traffic = tj.get(args.workload, {}).get(key)
-        except Exception:
-            traffic = None
+    dom_key = f"{dom['la']}{dom['lb']}{dom['lc']}{dom['ld']}_{MODE_NAMES[dom['mode']]}_G{dom['G']}_t{dom['team']}"
+    traffic = _profiled_traffic(args.workload, dom_key, dom["launches"])
 
     # end to end through the public host-buffer call: H2D of D, the build, D2H of J and K
     # (D, J and K in page-locked host memory: the copies run at full link speed)
@@ -425,6 +511,13 @@ def run_ours(args):
     e2 = lambda J, K: 0.5 * float(np.sum(D * (J - 0.5 * K)))  # noqa: E731
     dE = e2(J_mix, K_mix) - e2(J64, K64)
     fp64_rate = info64["function_quartets"] * fp64_steps / (ms64 * 1e-3)
+    # the benchmark spec's recipe keeps the Boys function of the FP32 quartets in FP64: the same build
+    # with that option (its own bins), timed and compared on the same density
+    g.jk_autotune(D, reps=2, **dict(tune_kw, boys_fp64=True))
+    for _ in range(2):
+        g.jk_device(dD, dJ, dK, **dict(kw, boys_fp64=True))
+    msb, infob = timed(fp64_steps, boys_fp64=True)
+    dE_boys = e2(dJ.cpu().numpy(), dK.cpu().numpy()) - e2(J64, K64)
 
     scf = _scf_section(mess, args) if args.scf_molecules > 0 else None
     mlp = None
@@ -436,10 +529,13 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, threads, dt = _oracle_rate(mol, bpath, args.cpu_elements)
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{args.cpu_elements} sampled J/K elements of the same workload, each by its defining "
-                         f"sum over all (l, s): 2 n^2 integral evaluations per element ({dt:.1f} s of CPU work)"}
+        r, threads, dt, ev = _oracle_rate(mol, bpath, D, args.cpu_elements)
+        cpu = {"value": r, "unit": "function-quartet integrals/s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_elements} seeded J/K elements of the same workload and density, each by its "
+                         f"defining sum over all (l, s) with the same Schwarz screening: {ev} function-quartet "
+                         f"integrals in {dt:.1f} s (one evaluation per integral, the unit of work of the GPU "
+                         f"metric's unique function quartets)",
+               "full_build_h2o_sto3g": _oracle_full_h2o()}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -456,6 +552,10 @@ def run_ours(args):
         "shell_quartets_fp64_per_step": info["shell_quartets_fp64"],
         "shell_quartets_per_s": world * info["shell_quartets"] * args.steps / (max_ms * 1e-3),
         "energy_error_vs_fp64_Ha": dE,
+        "boys_fp64_variant": {"energy_error_vs_fp64_Ha": dE_boys, "ms_per_step": msb / fp64_steps,
+                              "value": infob["function_quartets"] * fp64_steps / (msb * 1e-3), "unit": UNIT,
+                              "note": "the same reduced-precision build with the Boys function of its FP32 "
+                                      "quartets evaluated in FP64 for T < 36"},
         "fp64_path": {"value": fp64_rate, "unit": UNIT, "ms_per_step": ms64 / fp64_steps,
                       "speedup_of_reduced_precision": fp64_rate and value / world / fp64_rate},
         "gpu_launches": int(info["kernel_launches"]) * args.steps,
@@ -465,7 +565,14 @@ def run_ours(args):
                      "kernel_launches": dom["launches"], "kernel_ms": dom["ms"],
                      "kernel_share": dom["ms"] / tot_ms,
                      "peak_source": f"measured FMA-chain peak of this GPU ({'FP64' if dom_fp64_pipe else 'FP32'})",
-                     "whole_build": {"achieved": tot_flops / (tot_ms * 1e-3) / 1e12, "ms": tot_ms}},
+                     "traffic_source": "ncu capture summarised in profiles/jk_dram_traffic.txt (null unless "
+                                       "taken with the current sources)",
+                     "whole_build": {"flops_per_step": tot_flops,
+                                     "achieved_serialised": tot_flops / (tot_ms * 1e-3) / 1e12,
+                                     "ms_serialised": tot_ms,
+                                     "achieved_concurrent": tot_flops / (max_ms / args.steps * 1e-3) / 1e12,
+                                     "frac_concurrent_of_fp32_peak":
+                                         tot_flops / (max_ms / args.steps * 1e-3) / 1e12 / fp32_peak}},
         "peaks_measured_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
         "e2e": {"value": fnq / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8,
                 "call": "mess_jk_build on page-locked host D, J, K (copies and synchronisation inside the timing)"},
@@ -494,10 +601,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water8", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="water32", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--fp64-tau", dest="fp64_tau", type=float, default=0.0)
-    ap.add_argument("--cpu-elements", dest="cpu_elements", type=int, default=320)
+    ap.add_argument("--cpu-elements", dest="cpu_elements", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-df32", action="store_true", help="evaluate the split quartets in FP64 instead of double-float")
     ap.add_argument("--breakdown", action="store_true")

@@ -103,6 +103,9 @@ typedef struct {
 typedef struct {
     double E_total, E_elec, E_nuc;
     int iterations, converged;
+    double E_iter;   /* total energy of the last iteration's own J/K build: with MESS_MIXED / MESS_FP32
+                        the reduced-precision energy, before the final full-precision evaluation that
+                        sets E_total; with MESS_FP64 equal to E_total */
 } mess_scf_result;
 
 /* Build the contracted Cartesian basis of a structure (paper Sec. 3 LCAO basis; Sec. 5.1 basisset)
@@ -153,7 +156,13 @@ mess_status mess_jk_build_device(const mess_basis* b, const double* dD, double* 
  * held until the process exits) instead of freshly allocated buffers; results equal mess_jk_build's.
  * Limits: single-molecule bases with n <= 256 (larger n: MESS_EINVAL with a message); the quartet
  * bins for these opts must already exist - a prior mess_jk_build / mess_jk_build_device call with
- * the same opts builds them, otherwise MESS_EINVAL.  The first call on each device looks up the
+ * the same opts builds them, otherwise MESS_EINVAL (invalid opts: MESS_EINVAL with their own message).
+ * That prior allocating call also creates, with the bins, the basis's FP32 / double-float copies of
+ * the density that MESS_MIXED and MESS_FP32 builds read; this call reuses them and allocates none.
+ * A mess_scf on the same basis changes which molecules the bins cover and so invalidates them: the
+ * next static call returns MESS_EINVAL until another allocating build with these opts has run.
+ * Every return after the first copy has been enqueued (errors included) synchronises
+ * opts->cuda_stream first, so the array is free when the call returns.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current), so make that first call
  * before any stream capture.  All calls share the array and it keeps the last call's contents:
  * calls that overlap on the GPU race on it - serialise them. */

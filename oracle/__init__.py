@@ -78,6 +78,7 @@ def lib():
         L.oracle_jk_elements.argtypes = fn_args + [ip, ctypes.c_int, dp, ctypes.c_double, dp,
                                                    ctypes.c_int, ip, ip, dp, dp]
         L.oracle_num_threads.restype = ctypes.c_int
+        L.oracle_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
 
@@ -92,6 +93,11 @@ def _i(a):
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (n <= 0: every processor)."""
+    lib().oracle_set_num_threads(int(n))
 
 
 # ----------------------------------------------------------------------------- Boys function

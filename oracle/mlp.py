@@ -8,8 +8,9 @@ product, back-propagated products) are rounded the same way, so the GPU's FP32 a
 compared with exact FP64 sums; with ``bf16=False`` it is the exact-arithmetic network used by the
 finite-difference pin.
 
-parity: pinned by tests/test_oracle_mlp.py (central finite differences of the loss; descriptor
-closed forms for a diatomic; frame orthonormality).
+parity: pinned by tests/test_oracle_mlp.py (the loss and two gradient entries of a hand-set network
+worked out by hand; central finite differences of the loss; descriptor closed forms for a diatomic;
+frame orthonormality; the atomic target block equal to the average over the cube's rotations).
 """
 from __future__ import annotations
 

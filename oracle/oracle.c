@@ -464,6 +464,18 @@ void oracle_jk_elements(int nfn, const double *center, const int *lmn, const int
     }
 }
 
+/* Threads of the OpenMP loops (n <= 0: the runtime's default).  Scheduling only: the sums of
+ * every loop above are the same whatever the thread count. */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n <= 0) n = omp_get_num_procs();
+    omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

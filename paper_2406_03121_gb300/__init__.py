@@ -73,7 +73,7 @@ class mess_scf_opts(ctypes.Structure):
 
 class mess_scf_result(ctypes.Structure):
     _fields_ = [("E_total", ctypes.c_double), ("E_elec", ctypes.c_double), ("E_nuc", ctypes.c_double),
-                ("iterations", ctypes.c_int), ("converged", ctypes.c_int)]
+                ("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("E_iter", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -258,6 +258,29 @@ def _linear_scan(n_values, defs_uses, pinned=()):
     return slot, nslots
 
 
+def check_program(pr, nvi=None):
+    """Every slot an op program names lies inside the arrays the kernels declare for it (V: nvi
+    slots, default nv; H: nh slots), the contracted values fill H's first nacc slots, the base
+    values read F[m] with m <= L, and every field fits its bit width in the encoded words."""
+    nv, nh, nacc, L = pr["nv"], pr["nh"], pr["nacc"], pr["L"]
+    nvi = nv if nvi is None else nvi
+    assert nacc <= nh and nv <= nvi, (nacc, nh, nv, nvi)
+    assert nvi < 1 << 16 and nh < 1 << 16
+    for (kind, t, s1, s2, s3, s4, s5, d, m1, m2) in pr["vrr"]:
+        assert 0 <= t < nv and 0 <= d < 3 and 0 <= m1 < 16 and 0 <= m2 < 16
+        if kind == 0:
+            assert 0 <= s1 <= L
+        elif kind == 3:
+            assert 0 <= s1 < nacc
+        else:
+            assert kind in (1, 2) and all(0 <= x < nv for x in (s1, s2, s3, s4, s5))
+    for (t, s1, s2, d, side) in pr["hrr"]:
+        assert 0 <= t < nh and 0 <= s1 < nh and 0 <= s2 < nh and 0 <= d < 3 and side in (0, 1)
+    assert len(pr["fin"]) == pr["na"] * pr["nb"] * pr["nc"] * pr["nd"]
+    assert all(0 <= f < nh for f, _ in pr["fin"])
+    return pr
+
+
 def build_program(cls):
     (la, lb), (lc, ld) = cls
     v = VRR(la, lb, lc, ld)
@@ -377,8 +400,8 @@ def build_program(cls):
                 free.append(hslot[u])
     hrr_ops = [(hslot[t], hslot[s1], hslot[s2], d, side) for (t, s1, s2, d, side) in hops]
     fin = [(hslot[fv], sc) for fv, sc in finals]
-    return dict(vrr=vrr_ops, nv=nv, hrr=hrr_ops, nh=nh, fin=fin, nacc=nacc, L=la + lb + lc + ld,
-                na=ncart(la), nb=ncart(lb), nc=ncart(lc), nd=ncart(ld))
+    return check_program(dict(vrr=vrr_ops, nv=nv, hrr=hrr_ops, nh=nh, fin=fin, nacc=nacc, L=la + lb + lc + ld,
+                              na=ncart(la), nb=ncart(lb), nc=ncart(lc), nd=ncart(ld)))
 
 
 def _level_alloc(values, deflev, lastlev, pinned_slots=None, pinned_end=()):
@@ -534,8 +557,10 @@ def build_team_program(cls):
         hlev.append(len(hprog))
     fin = [(hslot[f], sc) for f, sc in finals]
     nint = len(fin)
-    return dict(vrr=vops, vlev=vlev, nv=nv, hrr=hprog, hlev=hlev, nh=nh, fin=fin, nacc=nacc,
-                L=la + lb + lc + ld, nint=nint, na=ncart(la), nb=ncart(lb), nc=ncart(lc), nd=ncart(ld))
+    pr = dict(vrr=vops, vlev=vlev, nv=nv, hrr=hprog, hlev=hlev, nh=nh, fin=fin, nacc=nacc,
+              L=la + lb + lc + ld, nint=nint, na=ncart(la), nb=ncart(lb), nc=ncart(lc), nd=ncart(ld))
+    # the warp/block kernels store the final integrals over the V region: nvi = max(nv, nint) slots
+    return check_program(pr, nvi=max(nv, nint))
 
 
 def straight_line(info):

@@ -887,12 +887,11 @@ static cudaGraphExec_t jk_capture(mess_basis* b, const mess_jk_opts& o, const do
     return exec;
 }
 
-// Argument checks shared by the J/K entry points, and the quartet bins for the options.
-static mess_status jk_prepare(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
-                              mess_jk_opts* out)
+// The J/K options checked and reduced to what selects the quartet bins: screening threshold tau,
+// split threshold tau64 (0 unless split == 2) and split (0: every quartet in FP64, 1: every quartet
+// in FP32, 2: FP64-class above tau64 and FP32 below).  Shared by the builds and the bins query.
+static mess_status jk_options(const mess_jk_opts* opts, mess_jk_opts* out, double* tau64_out, int* split_out)
 {
-    if (!b || !dD || !dJ || !dK) { mess_set_error("null argument"); return MESS_EINVAL; }
-    if (dD == dJ || dD == dK || dJ == dK) { mess_set_error("D, J and K must be distinct buffers"); return MESS_EINVAL; }
     mess_jk_opts o{};
     if (opts) o = *opts;
     if (o.prec != MESS_FP64 && o.prec != MESS_MIXED && o.prec != MESS_FP32) {
@@ -906,7 +905,22 @@ static mess_status jk_prepare(mess_basis* b, const double* dD, double* dJ, doubl
     else if (o.prec == MESS_FP32) split = 1;
     if (split != 2) tau64 = 0.0;
     *out = o;
-    return mess_ensure_bins(b, o.schwarz_tau, tau64, split);
+    *tau64_out = tau64;
+    *split_out = split;
+    return MESS_OK;
+}
+
+// Argument checks shared by the J/K entry points, and the quartet bins for the options.
+static mess_status jk_prepare(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
+                              mess_jk_opts* out)
+{
+    if (!b || !dD || !dJ || !dK) { mess_set_error("null argument"); return MESS_EINVAL; }
+    if (dD == dJ || dD == dK || dJ == dK) { mess_set_error("D, J and K must be distinct buffers"); return MESS_EINVAL; }
+    double tau64 = 0.0;
+    int split = 0;
+    mess_status st = jk_options(opts, out, &tau64, &split);
+    if (st != MESS_OK) return st;
+    return mess_ensure_bins(b, out->schwarz_tau, tau64, split);
 }
 
 static mess_status jk_run(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
@@ -1019,17 +1033,16 @@ mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* 
     return jk_run(b, dD, dJ, dK, opts, info, nullptr, 0, nullptr, graphs);
 }
 
-bool mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts)
+mess_status mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts, bool* ready)
 {
     mess_jk_opts o{};
-    if (opts) o = *opts;
-    double tau64 = o.fp64_tau == 0.0 ? MESS_DEFAULT_FP64_TAU : o.fp64_tau;
+    double tau64 = 0.0;
     int split = 0;
-    if (o.prec == MESS_MIXED) split = tau64 > 0.0 ? 2 : 1;
-    else if (o.prec == MESS_FP32) split = 1;
-    if (split != 2) tau64 = 0.0;
+    mess_status st = jk_options(opts, &o, &tau64, &split);
+    if (st != MESS_OK) return st;
     const BinSet& B = b->bins;
-    return B.tau == o.schwarz_tau && B.tau64 == tau64 && B.split == split && B.active_version == b->active_version;
+    *ready = B.tau == o.schwarz_tau && B.tau64 == tau64 && B.split == split && B.active_version == b->active_version;
+    return MESS_OK;
 }
 
 extern "C" mess_status mess_jk_profile(const mess_basis* bc, const double* dD, double* dJ, double* dK,

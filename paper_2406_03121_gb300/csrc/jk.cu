@@ -48,7 +48,11 @@ cudaError_t mess_launch_convert_density(const double* D, float* D32, float2* Ddf
 {
     if (count <= 0 || (!D32 && !Ddf)) return cudaSuccess;
     const int T = 256;
-    const long long blocks = std::min<long long>((count + T - 1) / T, 4LL * 152);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long blocks = std::min<long long>((count + T - 1) / T, 4LL * std::max(1, sms));
     k_convert_density<<<(unsigned)blocks, T, 0, s>>>(D, D32, Ddf, count);
     return cudaGetLastError();
 }

@@ -61,24 +61,35 @@ extern "C" mess_status mess_jk_build_static(const mess_basis* bc, const double* 
                        n, MESS_STATIC_NMAX);
         return MESS_EINVAL;
     }
-    if (!mess_jk_bins_ready(b, opts)) {
+    bool ready = false;
+    mess_status st = mess_jk_bins_ready(b, opts, &ready);
+    if (st != MESS_OK) return st;
+    if (!ready) {
         mess_set_error("mess_jk_build_static: the quartet bins for these options are not built yet; call "
                        "mess_jk_build or mess_jk_build_device once with the same options first");
         return MESS_EINVAL;
     }
     double* w = nullptr;
-    mess_status st = static_workspace(&w);
+    st = static_workspace(&w);
     if (st != MESS_OK) return st;
     mess_jk_opts o{};
     if (opts) o = *opts;
     cudaStream_t s = (cudaStream_t)o.cuda_stream;
     const size_t nn = (size_t)n * n;
     double *dD = w, *dJ = w + nn, *dK = w + 2 * nn;
-    MESS_CUDA_TRY(cudaMemcpyAsync(dD, D, nn * sizeof(double), cudaMemcpyHostToDevice, s));
-    st = mess_jk_packed(b, dD, dJ, dK, &o, info, /*graphs=*/false);
+    cudaError_t e = cudaMemcpyAsync(dD, D, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        st = mess_jk_packed(b, dD, dJ, dK, &o, info, /*graphs=*/false);
+        if (st == MESS_OK) {
+            e = cudaMemcpyAsync(J, dJ, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(K, dK, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
+        }
+    }
+    // whatever happened after the first copy was enqueued, the array is free again only once the
+    // stream has drained: the next call (on any stream) may then use it
+    const cudaError_t es = cudaStreamSynchronize(s);
     if (st != MESS_OK) return st;
-    MESS_CUDA_TRY(cudaMemcpyAsync(J, dJ, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
-    MESS_CUDA_TRY(cudaMemcpyAsync(K, dK, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
-    MESS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) { mess_set_error("mess_jk_build_static: %s", cudaGetErrorString(e)); return MESS_ECUDA; }
     return MESS_OK;
 }

@@ -172,8 +172,9 @@ mess_status mess_atoms_basis(const mess_basis* b, std::vector<int>& elements, me
 mess_status mess_scf_batch_density(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* dD);
 // learned guess: predicted D0 of every molecule of b (device, packed) (mlp.cu)
 mess_status mess_mlp_guess_device(const mess_mlp* m, const mess_basis* b, double* dD0, cudaStream_t s);
-// whether the quartet bins for these options are built (a J/K build with them would not allocate)
-bool mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts);
+// whether the quartet bins for these options are built (a J/K build with them would not allocate);
+// MESS_EINVAL for invalid options (checked first)
+mess_status mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts, bool* ready);
 // J/K on packed device matrices of (possibly batched) bases (host.cu)
 mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
                            mess_jk_info* info, bool graphs = true);

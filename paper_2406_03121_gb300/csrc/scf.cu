@@ -684,6 +684,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
                     res[m].E_elec = E[m];
                     res[m].E_nuc = Enuc[m];
                     res[m].E_total = E[m] + Enuc[m];
+                    res[m].E_iter = res[m].E_total;
                     res[m].iterations = it;
                     res[m].converged = 1;
                 }
@@ -710,6 +711,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
             res[m].E_elec = E[m];
             res[m].E_nuc = Enuc[m];
             res[m].E_total = E[m] + Enuc[m];
+            res[m].E_iter = res[m].E_total;
             res[m].iterations = iters[m];
             res[m].converged = 0;
         }

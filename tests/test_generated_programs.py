@@ -85,9 +85,13 @@ def _hrr_op(op, Hr, Hw, AB, CD):
 
 
 def _run(prog, team, pb, pk, L):
+    """Interpret a program with V and H sized exactly as the kernels declare them (a slot past the
+    end raises IndexError here; on the device it would read or overwrite a neighbouring array)."""
     x = _vrr_inputs(pb, pk, L)
-    V = np.full(max(prog["nv"], 1), np.nan)
-    H = np.zeros(max(prog["nh"], prog["nacc"], 1))
+    nvi = max(prog["nv"], prog["nint"]) if team else prog["nv"]
+    V = np.full(nvi, np.nan)
+    assert prog["nh"] >= prog["nacc"]
+    H = np.zeros(prog["nh"])
     H[prog["nacc"]:] = np.nan
     if team:
         # lane-parallel levels: every op of a level sees the values from before the level
@@ -119,6 +123,11 @@ def _run(prog, team, pb, pk, L):
             _hrr_op(op, H, H, pb["AB"], pk["AB"])
     out = np.array([H[s] for s, _ in prog["fin"]])
     assert np.all(np.isfinite(out)), "a final integral reads a slot never written"
+    if team:
+        # the warp/block kernels store the final integrals over the V region before the digestion
+        for k, (s, _) in enumerate(prog["fin"]):
+            V[k] = H[s]
+        assert np.array_equal(V[:len(out)], out)
     return out
 
 
@@ -189,3 +198,47 @@ def test_component_scales(cls):
                     want = fac(la, a) * fac(lb, b) * fac(lc, c) * fac(ld, e)
                     assert prog["fin"][k][1] == pytest.approx(want, rel=1e-15)
                     k += 1
+
+
+def _decode_vrr(w):
+    """One uint4 VRR word decoded as the kernels decode it."""
+    x, y, z, ww = w
+    return dict(kind=x & 3, d=(x >> 2) & 3, m1=(x >> 4) & 15, m2=(x >> 8) & 15, t=x >> 16,
+                s1=y & 0xFFFF, s2=y >> 16, s3=z & 0xFFFF, s4=z >> 16, s5=ww)
+
+
+@pytest.mark.parametrize("cls", CLASSES, ids=[GEN.tag(c) for c in CLASSES])
+def test_program_slots_in_bounds(cls):
+    """Every slot index a program names is below the size of the array the kernel declares for it
+    (V: NV, or max(NV, NINT) in the warp/block kernels, which store the integrals over V; H: NH, whose
+    first NACC slots hold the contracted values), and the packed words the generator emits decode
+    back to the same fields."""
+    (la, lb), (lc, ld) = cls
+    L = la + lb + lc + ld
+    for prog, nvi in ((GEN.build_program(cls), None), (GEN.build_team_program(cls), "team")):
+        nv = max(prog["nv"], prog["nint"]) if nvi else prog["nv"]
+        nh, nacc = prog["nh"], prog["nacc"]
+        assert nacc <= nh
+        for op in prog["vrr"]:
+            kind, t, s1, s2, s3, s4, s5, d, m1, m2 = op
+            word = (kind | (d << 2) | (m1 << 4) | (m2 << 8) | (t << 16), s1 | (s2 << 16), s3 | (s4 << 16), s5)
+            assert all(0 <= w < 2 ** 32 for w in word)
+            dec = _decode_vrr(word)
+            assert (dec["kind"], dec["t"], dec["d"], dec["m1"], dec["m2"]) == (kind, t, d, m1, m2)
+            assert dec["t"] < prog["nv"]
+            if kind == 0:
+                assert dec["s1"] <= L                       # F[m], m <= L
+            elif kind == 3:
+                assert dec["s1"] < nacc                     # H[acc] += V[t]
+            else:
+                assert max(dec["s1"], dec["s2"]) < prog["nv"]
+                if m1:
+                    assert max(dec["s3"], dec["s4"]) < prog["nv"]
+                if m2:
+                    assert dec["s5"] < prog["nv"]
+        for (t, s1, s2, d, side) in prog["hrr"]:
+            wx, wy = t | (d << 16) | (side << 18), s1 | (s2 << 16)
+            assert (wx & 0xFFFF, (wx >> 16) & 3, (wx >> 18) & 1, wy & 0xFFFF, wy >> 16) == (t, d, side, s1, s2)
+            assert max(t, s1, s2) < nh
+        assert all(f < nh for f, _ in prog["fin"])
+        assert len(prog["fin"]) <= nv or not nvi

@@ -248,24 +248,6 @@ def test_jk_every_kernel_variant(mess, oracle_mod, G, team):
             assert abs(e(J, K) - e(Jr, Kr)) <= 2e-5
 
 
-def test_full_size_water8_sampled(mess, oracle_mod):
-    """(H2O)_8 / 6-31G* (152 functions) at tau = 1e-10: sampled J/K elements against the oracle."""
-    mol = mi.water_cluster(8, 12.0, 2002)
-    g, o = _pair(mess, oracle_mod, mol, "6-31gs")
-    assert g.nbf == 152
-    D = mi.random_symmetric_density(g.nbf, 2002)
-    Q = oracle_mod.schwarz(o)
-    rng = np.random.default_rng(0)
-    rows = rng.integers(0, g.nbf, 12)
-    cols = rng.integers(0, g.nbf, 12)
-    Jr, Kr = oracle_mod.jk_elements(o, D, rows, cols, tau=1e-10, Q=Q)
-    for prec, tol in (("fp64", 1e-8), ("mixed", 2e-5)):
-        J, K, info = g.jk(D, prec=prec, schwarz_tau=1e-10)
-        assert np.abs(J[rows, cols] - Jr).max() <= tol
-        assert np.abs(K[rows, cols] - Kr).max() <= tol
-        assert np.allclose(J, J.T) and np.allclose(K, K.T)
-
-
 def test_single_atom_and_errors(mess, oracle_mod, tmp_path):
     he = mi.Molecule("he", np.array([2], dtype=np.int32), np.zeros((1, 3)))
     g, o = _pair(mess, oracle_mod, he, "sto-3g")
@@ -282,23 +264,3 @@ def test_single_atom_and_errors(mess, oracle_mod, tmp_path):
     bad.write_text("element H\nS 2\n 1.0 1.0\n")
     with pytest.raises(mess.MessError):
         mess.Basis([1], [[0, 0, 0]], str(bad))
-
-
-def test_full_size_water32_sampled(mess, oracle_mod):
-    """(H2O)_32 / 6-31G* (608 functions), tau = 1e-10, the benchmark's reduced-precision
-    configuration (default split in double-float): sampled elements against the oracle's defining
-    sums, and the whole matrices' symmetry."""
-    mol = mi.water_cluster(32, 19.0, 2006)
-    g = mess.Basis.from_molecule(mol, mi.basis_path("6-31gs"))
-    assert g.nbf == 608
-    D = mi.random_symmetric_density(g.nbf, 2006)
-    J, K, info = g.jk(D, prec="mixed", schwarz_tau=1e-10, split_df32=True)
-    assert info["shell_quartets_fp64"] > 0
-    o = oracle_mod.basis_for(mol, mi.basis_path("6-31gs"))
-    Q = oracle_mod.schwarz(o)
-    rng = np.random.default_rng(32)
-    rows, cols = rng.integers(0, g.nbf, 4), rng.integers(0, g.nbf, 4)
-    Jr, Kr = oracle_mod.jk_elements(o, D, rows, cols, tau=1e-10, Q=Q)
-    assert np.abs(J[rows, cols] - Jr).max() <= 2e-5
-    assert np.abs(K[rows, cols] - Kr).max() <= 2e-5
-    assert np.allclose(J, J.T, atol=0) and np.allclose(K, K.T, atol=0)
