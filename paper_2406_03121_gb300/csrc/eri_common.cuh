@@ -98,7 +98,13 @@ template <typename R> struct PairTable {
     const int* __restrict__ mn;              // [nmol] basis functions of the molecule (row stride)
     const double* __restrict__ boys64;       // Boys grid, FP64
     const float* __restrict__ boys32;        // Boys grid, FP32
+    const float4* __restrict__ boys32v;      // FP32 Taylor rows per order L: [L][row] {F_L..F_L+3}, {F_L+4, exp(-T_k), 0, 0}
     const float2* __restrict__ boysdf;       // Boys grid, double-float (hi, lo)
+    // per molecule: 0 = left the computation (a converged molecule of a batched SCF): its quartets
+    // are skipped by the J/K kernels.  Null: every molecule takes part.
+    const unsigned char* __restrict__ active = nullptr;
+
+    __device__ __forceinline__ bool live(int pair) const { return !active || __ldg(active + __ldg(mol + pair)) != 0; }
 
     __device__ __forceinline__ PrimPair<R> load(int i) const
     {
@@ -179,27 +185,25 @@ template <int L> __device__ __forceinline__ void boys_large_f64(double T, double
     }
 }
 
-template <int L> __device__ __forceinline__ void boys_small_f32(float T, float* F, const float* __restrict__ c_boys32)
+template <int L> __device__ __forceinline__ void boys_small_f32(float T, float* F, const float4* __restrict__ tabv)
 {
     // nearest grid index without F2I / I2F conversions (those issue on the slow FP64 pipe): adding
     // 1.5 * 2^23 rounds T / dT to an integer held in the low mantissa bits (0 <= T / dT < 2^22)
     const float r = fmaf(T, (float)MESS_BOYS_INV_DT, 12582912.0f);
     const int k = __float_as_int(r) - 0x4B400000;
     const float x = (r - 12582912.0f) * (float)MESS_BOYS_DT - T;
-    const float* row = c_boys32 + (size_t)k * MESS_BOYS_NCOL;
-    if (L == 0) {
-        float s = __ldg(row + 4);
-#pragma unroll
-        for (int j = 4; j >= 1; --j) s = __ldg(row + j - 1) + s * x * (1.0f / j);
-        F[0] = s;
-        return;
-    }
-    float s = __ldg(row + L + 4);
-#pragma unroll
-    for (int j = 4; j >= 1; --j) s = __ldg(row + L + j - 1) + s * x * (1.0f / j);
+    // the five Taylor coefficients F_L..F_L+4 at T_k and exp(-T_k) in two 16-byte loads
+    const float4* row = tabv + ((size_t)L * MESS_BOYS_NROW + k) * 2;
+    const float4 a = __ldg(row), b = __ldg(row + 1);
+    float s = b.x;
+    s = a.w + s * x * 0.25f;
+    s = a.z + s * x * (1.0f / 3);
+    s = a.y + s * x * 0.5f;
+    s = a.x + s * x;
     F[L] = s;
+    if (L == 0) return;
     const float ex = 1.0f + x * (1.0f + x * (0.5f + x * (1.0f / 6 + x * (1.0f / 24 + x * (1.0f / 120)))));
-    const float e = __ldg(row + MESS_BOYS_NF) * ex;
+    const float e = b.y * ex;
     const float t2 = 2.0f * T;
 #pragma unroll
     for (int m = L; m >= 1; --m) F[m - 1] = (t2 * F[m] + e) * (1.0f / (2 * m - 1));
@@ -288,7 +292,7 @@ template <> __device__ __forceinline__ void boys_eval<double, 0, 0>(double T, do
     }                                                                                             \
     template <> __device__ __forceinline__ void boys_eval<float, LL, 2>(float T, float* F,        \
                                                                        const PairTable<float>& P) \
-    { if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<LL>(T, F, P.boys32); else boys_large_f32<LL>(T, F); } \
+    { if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<LL>(T, F, P.boys32v); else boys_large_f32<LL>(T, F); } \
     template <> __device__ __forceinline__ void boys_eval<df32, LL, 3>(df32 T, df32* F,           \
                                                                       const PairTable<df32>& P)   \
     { if (T < MESS_BOYS_TMAX64) boys_small_df<LL>(T, F, P.boysdf); else boys_large_df<LL>(T, F); }
@@ -308,13 +312,21 @@ template <> __device__ __forceinline__ void boys_eval<float, 0, 1>(float T, floa
     else boys_large_f32<0>(T, F);
 }
 template <> __device__ __forceinline__ void boys_eval<float, 0, 2>(float T, float* F, const PairTable<float>& P)
-{ if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<0>(T, F, P.boys32); else boys_large_f32<0>(T, F); }
+{ if (T < (float)MESS_BOYS_TMAX32) boys_small_f32<0>(T, F, P.boys32v); else boys_large_f32<0>(T, F); }
 template <> __device__ __forceinline__ void boys_eval<df32, 0, 3>(df32 T, df32* F, const PairTable<df32>& P)
 { if (T < MESS_BOYS_TMAX64) boys_small_df<0>(T, F, P.boysdf); else boys_large_df<0>(T, F); }
 
-__device__ __forceinline__ double prefactor_sqrt(double rz) { return sqrt(rz); }
-__device__ __forceinline__ float prefactor_sqrt(float rz) { return sqrtf(rz); }
-__device__ __forceinline__ df32 prefactor_sqrt(df32 rz) { return df_sqrt(rz); }
+// 1/(zeta + eta) and its square root (the prefactor's 1/sqrt(zeta + eta)).  FP32: one reciprocal
+// square root (a few ulp, within the FP32 path's rounding) instead of a division and a square root.
+__device__ __forceinline__ void recip_and_sqrt(double s, double& rz, double& sq) { rz = 1.0 / s; sq = sqrt(rz); }
+__device__ __forceinline__ void recip_and_sqrt(float s, float& rz, float& sq) { sq = rsqrtf(s); rz = sq * sq; }
+__device__ __forceinline__ void recip_and_sqrt(df32 s, df32& rz, df32& sq) { rz = df32(1.0f, 0.f) / s; sq = df_sqrt(rz); }
+
+// primitive loops of the straight-line FP32 kernels run two primitive quartets per iteration (more
+// independent loads in flight); FP64 and double-float keep one (register pressure)
+template <typename R> struct PrimUnroll { static constexpr int value = 1; };
+template <> struct PrimUnroll<float> { static constexpr int value = 2; };
+
 
 // ------------------------------------------------------------------------------------------
 // J/K accumulation.  For a unique shell quartet (ab|cd) (pair ab >= pair cd, a >= b, c >= d by
@@ -406,8 +418,12 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         const int i = find_bra(b, q);                                                  \
         const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));                            \
         const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);                                     \
+        /* quartets past the end or of a molecule that has left: no work; a warp without any    */ \
+        /* quartet to do leaves (lanes of a group share the quartet, so groups leave together)  */ \
+        const bool live = valid && P.live(bp);                                                      \
+        if (__all_sync(0xffffffffu, !live)) return;                                                 \
         R I[(NA) * (NB) * (NC) * (ND)];                                                             \
-        eri_##TAG<R, BMODE, G>(P, bp, kp, g, I);                                                    \
+        eri_##TAG<R, BMODE, G>(P, bp, kp, g, I, live);                                              \
         DigestCtx<R> c;                                                                              \
         {                                                                                           \
             const int m_ = __ldg(P.mol + bp);                                                       \
@@ -417,7 +433,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         (void)n;                                                                                    \
         c.fa = __ldg(P.fa + bp); c.fb = __ldg(P.fb + bp);                                           \
         c.fc = __ldg(P.fa + kp); c.fd = __ldg(P.fb + kp);                                           \
-        R s = valid ? R(1) : R(0);                                                                  \
+        R s = live ? R(1) : R(0);                                                                   \
         if (__ldg(P.same + bp)) s *= R(0.5);                                                        \
         if (__ldg(P.same + kp)) s *= R(0.5);                                                        \
         if (bp == kp) s *= R(0.5);                                                                  \
@@ -502,13 +518,13 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
                                             const uint4* __restrict__ vprog, const uint2* __restrict__ hprog,
                                             const int* __restrict__ fslot, const double* __restrict__ fscale,
                                             const float* __restrict__ fscale_hi, const float* __restrict__ fscale_lo,
-                                            R* I)
+                                            R* I, bool live)
 {
     R V[NV];
     R H[NH];
 #pragma unroll 1
     for (int k = 0; k < NACC; ++k) H[k] = R(0);
-    const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];
+    const int b0 = P.pp_off[bp], b1 = b0 + (live ? P.pp_n[bp] : 0);
     const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
     const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);
 #pragma unroll 1
@@ -517,13 +533,14 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
 #pragma unroll 1
         for (int ik = k0; ik < k1; ++ik) {
             const PrimPair<R> pk = P.load(ik);
-            const R rz = R(1) / (pb.zeta + pk.zeta);
+            R rz, srz;
+            recip_and_sqrt(pb.zeta + pk.zeta, rz, srz);
             const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;
             const R PQx = pb.PAx - pk.PAx + ACx, PQy = pb.PAy - pk.PAy + ACy, PQz = pb.PAz - pk.PAz + ACz;
             const R WPx = -roz * PQx, WPy = -roz * PQy, WPz = -roz * PQz;
             const R WQx = roe * PQx, WQy = roe * PQy, WQz = roe * PQz;
             const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);
-            const R pref = pb.K * pk.K * prefactor_sqrt(rz);
+            const R pref = pb.K * pk.K * srz;
             R F[L + 1];
             boys_eval<R, L, BMODE>(T, F, P);
 #pragma unroll
@@ -610,6 +627,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     const int i = find_bra(b, q);
     const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));
     const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);
+    if (!P.live(bp)) return;                         // the quartet's threads leave together
     for (int k = plane; k < NACC; k += TP) Hp[k] = R(0);
     team_sync<TP>();
     const int b0 = P.pp_off[bp], nbp = P.pp_n[bp];
@@ -621,13 +639,14 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
         const PrimPair<R> pb = P.load(ib);
         {
             const PrimPair<R> pk = P.load(ik);
-            const R rz = R(1) / (pb.zeta + pk.zeta);
+            R rz, srz;
+            recip_and_sqrt(pb.zeta + pk.zeta, rz, srz);
             const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;
             const R PQx = pb.PAx - pk.PAx + ACx, PQy = pb.PAy - pk.PAy + ACy, PQz = pb.PAz - pk.PAz + ACz;
             const R WPx = -roz * PQx, WPy = -roz * PQy, WPz = -roz * PQz;
             const R WQx = roe * PQx, WQy = roe * PQy, WQz = roe * PQz;
             const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);
-            const R pref = pb.K * pk.K * prefactor_sqrt(rz);
+            const R pref = pb.K * pk.K * srz;
             R F[L + 1];
             boys_eval<R, L, BMODE>(T, F, P);
 #pragma unroll

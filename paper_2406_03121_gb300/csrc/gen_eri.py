@@ -563,6 +563,10 @@ def build_team_program(cls):
     return check_program(pr, nvi=max(nv, nint))
 
 
+# straight-line classes with at most this many VRR entries unroll their FP32 primitive loop by two
+PRIM_UNROLL_MAX_VRR = 24
+
+
 def straight_line(info):
     """classes emitted as straight-line register code (the rest run the op-program kernel)"""
     return info["nacc"] <= 96 and info["nvrr"] <= 280
@@ -584,17 +588,18 @@ def emit_class_straight(cls):
     lines = []
     lines.append(f"// ---- class ({la}{lb}|{lc}{ld}): {len(v.order)} VRR entries, {nacc} contracted, {nint} integrals")
     lines.append(f"template <typename R, int BMODE, int G>")
-    lines.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I)")
+    lines.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I, bool live = true)")
     lines.append("{")
     lines.append(f"    R acc[{nacc}];")
     lines.append(f"#pragma unroll")
     lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = R(0);")
-    lines.append("    const int b0 = P.pp_off[bp], b1 = b0 + P.pp_n[bp];")
+    lines.append("    const int b0 = P.pp_off[bp], b1 = b0 + (live ? P.pp_n[bp] : 0);   // !live: no primitive work")
     lines.append("    const int k0 = P.pp_off[kp], nk = P.pp_n[kp], k1 = k0 + nk;")
     lines.append("    // A - C in FP64, then P - Q = (P - A) - (Q - C) + (A - C): no absolute coordinates in R")
     lines.append("    const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);")
     body = []
-    body.append("            const R rz = R(1) / (pb.zeta + pk.zeta);")
+    body.append("            R rz, srz;")
+    body.append("            recip_and_sqrt(pb.zeta + pk.zeta, rz, srz);")
     body.append("            const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;")
     body.append("            const R oo2z = pb.oo2z, oo2e = pk.oo2z;")
     body.append("            (void)roe; (void)roz; (void)oo2ze; (void)oo2z; (void)oo2e;")
@@ -606,7 +611,7 @@ def emit_class_straight(cls):
     body.append("            (void)PAx; (void)PAy; (void)PAz; (void)QCx; (void)QCy; (void)QCz;")
     body.append("            (void)WPx; (void)WPy; (void)WPz; (void)WQx; (void)WQy; (void)WQz;")
     body.append("            const R T = pb.zeta * roz * (PQx * PQx + PQy * PQy + PQz * PQz);")
-    body.append("            const R pref = pb.K * pk.K * prefactor_sqrt(rz);")
+    body.append("            const R pref = pb.K * pk.K * srz;")
     body.append(f"            R F[{L + 1}];")
     body.append(f"            boys_eval<R, {L}, BMODE>(T, F, P);")
     body.append("#pragma unroll")
@@ -619,7 +624,7 @@ def emit_class_straight(cls):
     lines.append("#pragma unroll 1")
     lines.append("    for (int ib = b0; ib < b1; ++ib) {")
     lines.append("        const PrimPair<R> pb = P.load(ib);")
-    lines.append("#pragma unroll 1")
+    lines.append(f"#pragma unroll ({'PrimUnroll<R>::value' if len(v.order) <= PRIM_UNROLL_MAX_VRR else 1})")
     lines.append("        for (int ik = k0; ik < k1; ++ik) {")
     lines.append("            const PrimPair<R> pk = P.load(ik);")
     lines += body
@@ -695,13 +700,13 @@ def emit_class(cls):
     L.append(f"__device__ const float fscaleh_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(h) + "f" for h in his) + "};")
     L.append(f"__device__ const float fscalel_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(l) + "f" for l in los) + "};")
     L.append("template <typename R, int BMODE, int G>")
-    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I)")
+    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I, bool live = true)")
     L.append("{")
     L.append("    static_assert(G == 1, \"op-program classes run one thread per quartet\");")
     L.append("    (void)g;")
     L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
              f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kp, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, "
-             f"fscaleh_{t}, fscalel_{t}, I);")
+             f"fscaleh_{t}, fscalel_{t}, I, live);")
     L.append("}")
     return "\n".join(L) + "\n", info
 

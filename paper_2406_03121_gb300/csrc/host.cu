@@ -494,6 +494,16 @@ static mess_status build_pairs(mess_basis* b)
     MESS_CUDA_TRY(b->d_boys64.upload(tab));
     std::vector<float> tab32(tab.begin(), tab.end());
     MESS_CUDA_TRY(b->d_boys32.upload(tab32));
+    // FP32 Taylor rows per order L (two float4 per grid row): F_L..F_L+3 | F_L+4, exp(-T_k), 0, 0
+    std::vector<float4> tabv((size_t)MESS_BOYS_NL * MESS_BOYS_NROW * 2);
+    for (int L = 0; L < MESS_BOYS_NL; ++L)
+        for (int k = 0; k < MESS_BOYS_NROW; ++k) {
+            const double* row = tab.data() + (size_t)k * MESS_BOYS_NCOL;
+            float4* o = tabv.data() + ((size_t)L * MESS_BOYS_NROW + k) * 2;
+            o[0] = make_float4((float)row[L], (float)row[L + 1], (float)row[L + 2], (float)row[L + 3]);
+            o[1] = make_float4((float)row[L + 4], (float)row[MESS_BOYS_NF], 0.f, 0.f);
+        }
+    MESS_CUDA_TRY(b->d_boys32v.upload(tabv));
     std::vector<float2> tabdf(tab.size());
     for (size_t i = 0; i < tab.size(); ++i) {
         tabdf[i].x = (float)tab[i];
@@ -522,6 +532,7 @@ static mess_status build_pairs(mess_basis* b)
     b->P64.mn = b->P32.mn = b->d_mol_n.p;
     b->P64.boys64 = b->P32.boys64 = b->d_boys64.p;
     b->P64.boys32 = b->P32.boys32 = b->d_boys32.p;
+    b->P64.boys32v = b->P32.boys32v = b->d_boys32v.p;
     b->P64.boysdf = b->P32.boysdf = b->d_boysdf.p;
     // the double-float table shares every per-pair array with the others
     b->Pdf.pp = b->d_ppdf.p;
@@ -529,6 +540,7 @@ static mess_status build_pairs(mess_basis* b)
     b->Pdf.fb = b->P64.fb; b->Pdf.same = b->P64.same; b->Pdf.C = b->P64.C; b->Pdf.Cf = b->P64.Cf;
     b->Pdf.ABf = b->P64.ABf; b->Pdf.mol = b->P64.mol; b->Pdf.mbase = b->P64.mbase; b->Pdf.mn = b->P64.mn;
     b->Pdf.boys64 = b->d_boys64.p; b->Pdf.boys32 = b->d_boys32.p; b->Pdf.boysdf = b->d_boysdf.p;
+    b->Pdf.boys32v = b->d_boys32v.p;
     // shells for the one-electron kernels
     std::vector<int> sl, sK, sf0, spoff;
     std::vector<double> sR, sal, sco;
@@ -603,7 +615,7 @@ void mess_free_basis(mess_basis* b)
 {
     b->d_pp64.free(); b->d_pp32.free(); b->d_ppdf.free(); b->d_boysdf.free(); b->d_pp_off.free(); b->d_pp_n.free(); b->d_fa.free();
     b->d_fb.free(); b->d_same.free(); b->d_AB.free(); b->d_Ccen.free(); b->d_ABf.free(); b->d_Cf.free(); b->d_Q.free(); b->d_boys64.free();
-    b->d_boys32.free(); b->d_Z.free(); b->d_xyz.free(); b->d_shell_l.free(); b->d_shell_K.free();
+    b->d_boys32.free(); b->d_boys32v.free(); b->d_Z.free(); b->d_xyz.free(); b->d_shell_l.free(); b->d_shell_K.free();
     b->d_shell_f0.free(); b->d_shell_poff.free(); b->d_shell_R.free(); b->d_shell_alpha.free();
     b->d_shell_coef.free(); b->d_fscale.free(); b->d_pair_a.free(); b->d_pair_b.free();
     b->d_pair_mol.free(); b->d_mol_n.free(); b->d_mol_atom_off.free(); b->d_mol_atom_n.free();
@@ -1031,6 +1043,40 @@ mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* 
                            mess_jk_info* info, bool graphs)
 {
     return jk_run(b, dD, dJ, dK, opts, info, nullptr, 0, nullptr, graphs);
+}
+
+mess_status mess_jk_ensure_bins(mess_basis* b, const mess_jk_opts* opts)
+{
+    static double dummy[3];
+    mess_jk_opts o{};
+    return jk_prepare(b, dummy, dummy + 1, dummy + 2, opts, &o);
+}
+
+mess_status mess_jk_enqueue_only(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts)
+{
+    mess_jk_opts o{};
+    double tau64 = 0.0;
+    int split = 0;
+    mess_status st = jk_options(opts, &o, &tau64, &split);
+    if (st != MESS_OK) return st;
+    const BinSet& B = b->bins;
+    if (!(B.tau == o.schwarz_tau && B.tau64 == tau64 && B.split == split && B.active_version == b->active_version)) {
+        mess_set_error("J/K enqueue: the quartet bins for these options are not built");
+        return MESS_EINVAL;
+    }
+    bool need32 = false, needdf = false;
+    for (const BinPart& p : b->bins.parts) {
+        const int m = part_mode(p, o);
+        if (m == MESS_MODE_FP32 || m == MESS_MODE_MIXED) need32 = true;
+        else if (m == MESS_MODE_DF32) needdf = true;
+    }
+    if ((need32 && !b->d_D32.p) || (needdf && !b->d_Ddf.p)) { mess_set_error("density copies missing"); return MESS_ECUDA; }
+    StreamPool* pool = nullptr;
+    MESS_CUDA_TRY(get_pool(&pool));
+    std::unique_lock<std::mutex> lk(pool->mu);
+    mess_jk_info inf{};
+    return jk_enqueue(b, o, dD, dJ, dK, (cudaStream_t)o.cuda_stream, need32, needdf,
+                      b->bins.parts.size() > 1 ? pool : nullptr, nullptr, &inf);
 }
 
 mess_status mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts, bool* ready)

@@ -11,6 +11,7 @@
 #define MESS_BOYS_NF 16
 #define MESS_BOYS_NCOL (MESS_BOYS_NF + 1)
 #define MESS_BOYS_NROW 362
+#define MESS_BOYS_NL 9            // orders L = 0..8 of the FP32 Taylor rows (L = la+lb+lc+ld <= 8)
 
 #define MESS_LMAX 2               // s, p, Cartesian d
 #define MESS_NUM_PCLASS 6         // pair classes (la,lb): ss ps pp ds dp dd

@@ -130,6 +130,7 @@ struct mess_basis {
     DevBuf<float> d_ABf, d_Cf;
     DevBuf<double> d_boys64;
     DevBuf<float> d_boys32;
+    DevBuf<float4> d_boys32v;
     DevBuf<int> d_Z;
     DevBuf<double> d_xyz;
     DevBuf<int> d_shell_l, d_shell_K, d_shell_f0, d_shell_poff;
@@ -179,3 +180,10 @@ mess_status mess_jk_bins_ready(const mess_basis* b, const mess_jk_opts* opts, bo
 mess_status mess_jk_packed(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts,
                            mess_jk_info* info, bool graphs = true);
 void mess_free_jk_graphs(mess_basis* b);
+// the quartet bins for these options, built if missing (may allocate; not under stream capture)
+mess_status mess_jk_ensure_bins(mess_basis* b, const mess_jk_opts* opts);
+// the launches of one J/K build on opts->cuda_stream and nothing else: no allocation, no event
+// shared with other builds and no cached graph, so that a caller's stream capture can record them.
+// The bins for the options must already exist (MESS_EINVAL otherwise).  The caller orders builds
+// on one basis (they share its reduced-precision density copies).
+mess_status mess_jk_enqueue_only(mess_basis* b, const double* dD, double* dJ, double* dK, const mess_jk_opts* opts);

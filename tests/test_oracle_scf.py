@@ -133,3 +133,17 @@ def test_scf_guess_independence(oracle_mod):
     r2 = oracle_mod.scf(b, D0=D0)
     assert r1.converged and r2.converged
     assert r2.E_total == pytest.approx(r1.E_total, abs=1e-9)
+
+
+def test_h2_dissociation_limit(oracle_mod):
+    """Minimal-basis RHF H2 dissociates to 2 h_11 + (11|11)/2 (one sigma_g orbital, cross terms
+    vanishing), approached as -1/(2R): at large R the neutral atoms' Coulomb terms cancel except half
+    of the inter-atomic electron repulsion.  h_11 = T_11 + V^(1)_11 and (11|11) from the printed
+    STO-3G values (zeta = 1.24): 2 (0.7600 - 1.2266) + 0.7746 / 2 = -0.5459."""
+    gold = json.load(open(GOLDEN))["h2"]
+    limit = 2.0 * (gold["T11"] + gold["V1_11"]) + 0.5 * gold["eri_1111"]
+    for R in (10.0, 20.0):
+        o = oracle_mod.basis_for(mi.h2(R), mi.basis_path("sto-3g"))
+        r = oracle_mod.scf(o)
+        assert r.converged
+        assert r.E_total + 0.5 / R == pytest.approx(limit, abs=3e-4)
