@@ -98,6 +98,13 @@ typedef struct {
     int split_df32;       /* see mess_jk_opts */
     const char* mlp_weights; /* MESS_GUESS_MLP: weight file of mess_mlp_save (unused otherwise) */
     void* cuda_stream;
+    double dens_tau;      /* density-weighted screening of the incremental Fock builds: a shell quartet is
+                             skipped when Q_ab Q_cd times the largest change of the density in the rows of
+                             its shells is below dens_tau (0: off, the default).  Each skipped contribution
+                             is below dens_tau, but they change from one iteration to the next: values
+                             above about 1e-13 can hold the commutator above conv_comm */
+    int xc;               /* energy functional: 0 Hartree-Fock (xc_method "hfx"), 1 LDA (Slater exchange +
+                             Perdew-Wang 1992 correlation), 2 PBE; see mess_xc for the grid */
 } mess_scf_opts;
 
 typedef struct {
@@ -176,6 +183,17 @@ mess_status mess_eri_tensor(const mess_basis* b, double* G);
 /* Schwarz factor of every shell pair as an nshell x nshell host matrix (symmetric). */
 mess_status mess_schwarz(const mess_basis* b, double* Q);
 
+/* Exchange-correlation energy and matrix of a density on the library's molecular grid (paper Sec. 5.1,
+ * xc_method "lda" / "pbe"; Kohn-Sham 1965).  Grid per atom: radial Gauss-Chebyshev (second kind) mapped
+ * by r = R (1 + x) / (1 - x) (R = 0.35 angstrom for H, half the Bragg-Slater radius otherwise: C 0.35,
+ * N 0.325, O 0.30), 50 points for H and 75 otherwise, times 16 Gauss-Legendre cos(theta) x 32 phi;
+ * Becke's fuzzy-cell partition between atoms.  xc: 1 LDA (Slater exchange, Perdew-Wang 1992
+ * correlation), 2 PBE.  D: host n x n (closed-shell total density); Exc (nullable): E_xc; V (nullable):
+ * host n x n, V_mn = dE_xc/dD_mn = sum_g w_g [v_rho phi_m phi_n + 2 v_sigma grad rho . grad(phi_m phi_n)];
+ * npts (nullable): grid points.  The grid and the basis functions' values are built on the first call
+ * and kept with the basis.  Errors: MESS_EINVAL, MESS_ENOMEM, MESS_ECUDA. */
+mess_status mess_xc(const mess_basis* b, int xc, const double* D, double* Exc, double* V, long long* npts);
+
 /* Closed-shell Roothaan SCF (paper Eq. 2, Sec. 3): Loewdin orthogonalisation, core-Hamiltonian
  * guess, Pulay DIIS on FDS - SDF, converged when |dE| < conv_E and max|FDS - SDF| < conv_comm.
  * Runs entirely on the GPU: one-electron integrals, Loewdin X (Jacobi eigensolver), the J/K builds of
@@ -185,6 +203,8 @@ mess_status mess_schwarz(const mess_basis* b, double* Q);
  * energy is that of the final density with one build in which every quartet runs in double-float
  * (split_df32) or FP64: the integrals' rounding leaves the energy, and the density's residual
  * error enters it only at second order.
+ * With opts->xc = 1 or 2 it is the Kohn-Sham SCF of that functional: F = H + J + V_xc and E_elec =
+ * tr(D H) + 1/2 tr(D J) + E_xc (the exchange matrix K is not used).
  * D_out (nullable): host n*n final density.  Errors: MESS_ENOCONV (res holds the last iterate),
  * MESS_EINVAL (odd electron count, MESS_GUESS_MLP without weights), MESS_ENOTIMPL (n > 256),
  * MESS_ENOMEM, MESS_ECUDA, MESS_ENUMERIC (singular overlap, non-finite energy). */
@@ -196,6 +216,41 @@ mess_status mess_scf(const mess_basis* b, const mess_scf_opts* opts, mess_scf_re
  * block per molecule; converged molecules drop out.  res: nmol entries (caller-owned).
  * Errors: as mess_scf; MESS_ENOCONV if any molecule did not converge. */
 mess_status mess_scf_batch(int nmol, mess_basis* const* bases, const mess_scf_opts* opts, mess_scf_result* res);
+
+/* Direct minimisation of the energy functional (paper Sec. 3: E(C) minimised subject to the
+ * orthonormality C^T S C = 1, Eqs. 4-5; Sec. 5.1 and 5.2: first-order optimisation with Adam, the
+ * constraint built in by a QR decomposition).  Per molecule the unconstrained parameters are an n x n
+ * matrix Z, starting from the identity: Z = Q R (Householder), C = X Q with X = S^-1/2, D =
+ * 2 C_occ C_occ^T, E(Z) = 1/2 sum D (H + F) + E_nuc with F = H + J(D) - K(D)/2 from the J/K build
+ * (prec, schwarz_tau, fp64_tau, boys_fp64, split_df32 as in mess_jk_opts), and dE/dZ = Q
+ * tril(Q^T G - G^T Q, -1) R^-T with G = X (4 F C_occ | 0).  Adam: m = b1 m + (1 - b1) g, v = b2 v +
+ * (1 - b2) g^2, Z -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+typedef struct {
+    mess_precision prec;
+    int steps;            /* Adam steps, default 200 when <= 0 */
+    double lr;            /* default 0.1 when <= 0 */
+    double beta1, beta2;  /* defaults 0.9, 0.999 when <= 0 */
+    double eps;           /* default 1e-8 when <= 0 */
+    double grad_tol;      /* converged when max |dE/dZ| at the final Z is below it; default 1e-5 */
+    double schwarz_tau;
+    double fp64_tau;
+    int boys_fp64;
+    int split_df32;
+    void* cuda_stream;
+    int xc;               /* 0 Hartree-Fock, 1 LDA, 2 PBE (as mess_scf_opts) */
+} mess_min_opts;
+
+/* One molecule; res->E_total etc. at the final Z, res->iterations = steps, res->converged as above.
+ * trace (nullable): steps doubles, the total energy at the parameters of each step (before its
+ * update).  Errors: MESS_ENOCONV (the gradient criterion failed; results still filled), MESS_EINVAL,
+ * MESS_ENOTIMPL (n > 256), MESS_ENUMERIC (singular R or a non-finite energy), MESS_ENOMEM, MESS_ECUDA. */
+mess_status mess_minimise(const mess_basis* b, const mess_min_opts* opts, mess_scf_result* res, double* trace);
+/* The same over every molecule of bases[0..nmol) at once (the paper's batch over conformations,
+ * Sec. 5.2: one set of launches per step for the whole batch; the loss is the sum of the molecules'
+ * energies, so each molecule follows its own Adam trajectory).  res: nmol entries; trace (nullable):
+ * steps x nmol doubles, row t holding every molecule's energy at step t. */
+mess_status mess_minimise_batch(int nmol, mess_basis* const* bases, const mess_min_opts* opts, mess_scf_result* res,
+                                double* trace);
 
 /* One kernel launch of a profiled J/K build. */
 typedef struct {

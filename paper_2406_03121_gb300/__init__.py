@@ -29,7 +29,7 @@ EXPORTED = [
     "mess_basis_create", "mess_basis_nbf", "mess_basis_nshell", "mess_basis_nelectron",
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
     "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
-    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_jk_profile", "mess_jk_autotune", "mess_jk_set_variant",
+    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_minimise", "mess_minimise_batch", "mess_xc", "mess_jk_profile", "mess_jk_autotune", "mess_jk_set_variant",
     "mess_jk_get_tuning", "mess_jk_set_tuning", "mess_boys_grid", "mess_profiler_range", "mess_fma_peak",
     "mess_last_error",
     "mess_mlp_num_params", "mess_mlp_create", "mess_mlp_destroy", "mess_mlp_get_params", "mess_mlp_set_params",
@@ -68,7 +68,15 @@ class mess_scf_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("guess", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("conv_E", ctypes.c_double), ("conv_comm", ctypes.c_double), ("diis_n", ctypes.c_int),
                 ("schwarz_tau", ctypes.c_double), ("fp64_tau", ctypes.c_double), ("boys_fp64", ctypes.c_int),
-                ("split_df32", ctypes.c_int), ("mlp_weights", ctypes.c_char_p), ("cuda_stream", ctypes.c_void_p)]
+                ("split_df32", ctypes.c_int), ("mlp_weights", ctypes.c_char_p), ("cuda_stream", ctypes.c_void_p),
+                ("dens_tau", ctypes.c_double), ("xc", ctypes.c_int)]
+
+
+class mess_min_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("steps", ctypes.c_int), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("grad_tol", ctypes.c_double),
+                ("schwarz_tau", ctypes.c_double), ("fp64_tau", ctypes.c_double), ("boys_fp64", ctypes.c_int),
+                ("split_df32", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("xc", ctypes.c_int)]
 
 
 class mess_scf_result(ctypes.Structure):
@@ -115,6 +123,12 @@ mess_scf = _sig("mess_scf", ctypes.c_int,
 mess_scf_batch = _sig("mess_scf_batch", ctypes.c_int,
                       [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(mess_scf_opts),
                        ctypes.POINTER(mess_scf_result)])
+mess_minimise = _sig("mess_minimise", ctypes.c_int,
+                     [_P, ctypes.POINTER(mess_min_opts), ctypes.POINTER(mess_scf_result), _DP])
+mess_minimise_batch = _sig("mess_minimise_batch", ctypes.c_int,
+                           [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(mess_min_opts),
+                            ctypes.POINTER(mess_scf_result), _DP])
+mess_xc = _sig("mess_xc", ctypes.c_int, [_P, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_longlong)])
 mess_jk_profile = _sig("mess_jk_profile", ctypes.c_int,
                        [_P, _P, _P, _P, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_part), ctypes.c_int,
                         ctypes.POINTER(ctypes.c_int)])
@@ -331,11 +345,32 @@ class Basis:
                "mess_jk_profile")
         return [parts[i].as_dict() for i in range(n.value)]
 
+    def xc(self, D, kind="lda"):
+        """E_xc and V_xc of a host density on the library's grid (see mess_xc); returns (E_xc, V, points)."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        V = np.zeros_like(D)
+        E = np.zeros(1)
+        npts = ctypes.c_longlong()
+        _check(mess_xc(self._h, XC[kind] if isinstance(kind, str) else int(kind), _dptr(D), _dptr(E), _dptr(V),
+                       ctypes.byref(npts)), "mess_xc")
+        return float(E[0]), V, npts.value
+
+    def minimise(self, **kw):
+        """Direct minimisation of this molecule's energy (see mess_minimise); returns (result dict,
+        energy per step, status)."""
+        o = min_opts(**kw)
+        r = mess_scf_result()
+        trace = np.zeros(o.steps)
+        st = mess_minimise(self._h, ctypes.byref(o), ctypes.byref(r), _dptr(trace))
+        if st not in (MESS_OK, MESS_ENOCONV):
+            _check(st, "mess_minimise")
+        return r.as_dict(), trace, st
+
     def scf(self, prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8, diis_n=8,
             schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, want_density=True, boys_fp64=False,
-            split_df32=False):
+            split_df32=False, dens_tau=0.0, xc="hf"):
         o = scf_opts(prec, guess, max_iter, conv_E, conv_comm, diis_n, schwarz_tau, fp64_tau, mlp_weights, stream,
-                     boys_fp64, split_df32)
+                     boys_fp64, split_df32, dens_tau, xc)
         res = mess_scf_result()
         D = np.zeros((self.nbf, self.nbf)) if want_density else None
         st = mess_scf(self._h, ctypes.byref(o), ctypes.byref(res), _dptr(D) if D is not None else None)
@@ -368,29 +403,54 @@ def fma_peak(stream=None):
     return a.value, b.value
 
 
+XC = {"hf": 0, "hfx": 0, "lda": 1, "pbe": 2}
+
+
 def scf_opts(prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8, diis_n=8,
              schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, boys_fp64=False,
-             split_df32=False) -> mess_scf_opts:
+             split_df32=False, dens_tau=0.0, xc="hf") -> mess_scf_opts:
     p = PRECISION[prec] if isinstance(prec, str) else int(prec)
     w = os.fsencode(mlp_weights) if mlp_weights else None
     return mess_scf_opts(p, int(guess), int(max_iter), float(conv_E), float(conv_comm), int(diis_n),
                          float(schwarz_tau), float(fp64_tau), int(bool(boys_fp64)), int(bool(split_df32)), w,
-                         _stream_handle(stream))
+                         _stream_handle(stream), float(dens_tau), XC[xc] if isinstance(xc, str) else int(xc))
 
 
 def scf_batch(bases, prec="fp64", guess=MESS_GUESS_CORE, max_iter=100, conv_E=1e-10, conv_comm=1e-8,
               diis_n=8, schwarz_tau=0.0, fp64_tau=0.0, mlp_weights=None, stream=None, boys_fp64=False,
-              split_df32=False):
+              split_df32=False, dens_tau=0.0, xc="hf"):
     """Batched SCF over many bases; returns a list of result dicts and the call's status."""
     n = len(bases)
     arr = (_P * n)(*[b.handle for b in bases])
     res = (mess_scf_result * n)()
     o = scf_opts(prec, guess, max_iter, conv_E, conv_comm, diis_n, schwarz_tau, fp64_tau, mlp_weights, stream,
-                 boys_fp64, split_df32)
+                 boys_fp64, split_df32, dens_tau, xc)
     st = mess_scf_batch(n, arr, ctypes.byref(o), res)
     if st not in (MESS_OK, MESS_ENOCONV):
         _check(st, "mess_scf_batch")
     return [r.as_dict() for r in res], st
+
+
+def min_opts(prec="fp64", steps=200, lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, grad_tol=1e-5, schwarz_tau=0.0,
+             fp64_tau=0.0, boys_fp64=False, split_df32=False, stream=None, xc="hf") -> mess_min_opts:
+    p = PRECISION[prec] if isinstance(prec, str) else int(prec)
+    return mess_min_opts(p, int(steps), float(lr), float(beta1), float(beta2), float(eps), float(grad_tol),
+                         float(schwarz_tau), float(fp64_tau), int(bool(boys_fp64)), int(bool(split_df32)),
+                         _stream_handle(stream), XC[xc] if isinstance(xc, str) else int(xc))
+
+
+def minimise_batch(bases, **kw):
+    """Direct minimisation (QR-orthonormalised parameters, Adam) of every basis at once; returns (list
+    of result dicts, energy trace as a steps x nmol array, status)."""
+    n = len(bases)
+    o = min_opts(**kw)
+    arr = (_P * n)(*[b.handle for b in bases])
+    res = (mess_scf_result * n)()
+    trace = np.zeros((o.steps, n))
+    st = mess_minimise_batch(n, arr, ctypes.byref(o), res, _dptr(trace))
+    if st not in (MESS_OK, MESS_ENOCONV):
+        _check(st, "mess_minimise_batch")
+    return [r.as_dict() for r in res], trace, st
 
 
 def _fptr(a: np.ndarray):

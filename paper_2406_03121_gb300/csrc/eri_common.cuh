@@ -103,8 +103,20 @@ template <typename R> struct PairTable {
     // per molecule: 0 = left the computation (a converged molecule of a batched SCF): its quartets
     // are skipped by the J/K kernels.  Null: every molecule takes part.
     const unsigned char* __restrict__ active = nullptr;
+    // Density-weighted screening of a build (null dmax: none): a shell quartet is skipped when
+    // Q_ab Q_cd max(dmax_ab, dmax_cd) < dtau, with dmax_p the largest |D_mn| over the rows m of the
+    // two shells of pair p.  Every density element a quartet's J/K terms read lies in one of those
+    // rows, so each skipped contribution is below dtau (the incremental Fock builds of an SCF, whose
+    // density changes shrink as it converges).
+    const float* __restrict__ Qf = nullptr;     // Schwarz factor per pair (FP32)
+    const float* __restrict__ dmax = nullptr;
+    float dtau = 0.f;
 
     __device__ __forceinline__ bool live(int pair) const { return !active || __ldg(active + __ldg(mol + pair)) != 0; }
+    __device__ __forceinline__ bool dens_ok(int bp, int kp) const
+    {
+        return !dmax || __ldg(Qf + bp) * __ldg(Qf + kp) * fmaxf(__ldg(dmax + bp), __ldg(dmax + kp)) >= dtau;
+    }
 
     __device__ __forceinline__ PrimPair<R> load(int i) const
     {
@@ -420,7 +432,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);                                     \
         /* quartets past the end or of a molecule that has left: no work; a warp without any    */ \
         /* quartet to do leaves (lanes of a group share the quartet, so groups leave together)  */ \
-        const bool live = valid && P.live(bp);                                                      \
+        const bool live = valid && P.live(bp) && P.dens_ok(bp, kp);                                 \
         if (__all_sync(0xffffffffu, !live)) return;                                                 \
         R I[(NA) * (NB) * (NC) * (ND)];                                                             \
         eri_##TAG<R, BMODE, G>(P, bp, kp, g, I, live);                                              \
@@ -627,7 +639,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     const int i = find_bra(b, q);
     const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));
     const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);
-    if (!P.live(bp)) return;                         // the quartet's threads leave together
+    if (!P.live(bp) || !P.dens_ok(bp, kp)) return;   // the quartet's threads leave together
     for (int k = plane; k < NACC; k += TP) Hp[k] = R(0);
     team_sync<TP>();
     const int b0 = P.pp_off[bp], nbp = P.pp_n[bp];

@@ -589,6 +589,13 @@ static mess_status build_schwarz(mess_basis* b)
     MESS_CUDA_TRY(cudaMemcpy(b->Q.data(), b->d_Q.p, sizeof(double) * b->npair, cudaMemcpyDeviceToHost));
     for (int p = 0; p < b->npair; ++p)
         if (!std::isfinite(b->Q[p])) { mess_set_error("non-finite Schwarz factor for pair %d", p); return MESS_ENUMERIC; }
+    {
+        // FP32 copy for the density-screening test (rounded up, so that the bound stays a bound)
+        std::vector<float> qf(std::max(1, b->npair), 0.f);
+        for (int p = 0; p < b->npair; ++p) qf[p] = nextafterf((float)b->Q[p], INFINITY);
+        MESS_CUDA_TRY(b->d_Qf.upload(qf));
+        b->P64.Qf = b->P32.Qf = b->Pdf.Qf = b->d_Qf.p;
+    }
     // lists per (class, primitive-count group): per molecule, pairs sorted by Q descending
     for (int c = 0; c < MESS_NUM_PCLASS; ++c) {
         for (int g = 0; g < MESS_NGROUP; ++g) {
@@ -614,7 +621,7 @@ static mess_status build_schwarz(mess_basis* b)
 void mess_free_basis(mess_basis* b)
 {
     b->d_pp64.free(); b->d_pp32.free(); b->d_ppdf.free(); b->d_boysdf.free(); b->d_pp_off.free(); b->d_pp_n.free(); b->d_fa.free();
-    b->d_fb.free(); b->d_same.free(); b->d_AB.free(); b->d_Ccen.free(); b->d_ABf.free(); b->d_Cf.free(); b->d_Q.free(); b->d_boys64.free();
+    b->d_fb.free(); b->d_same.free(); b->d_AB.free(); b->d_Ccen.free(); b->d_ABf.free(); b->d_Cf.free(); b->d_Q.free(); b->d_Qf.free(); b->d_boys64.free();
     b->d_boys32.free(); b->d_boys32v.free(); b->d_Z.free(); b->d_xyz.free(); b->d_shell_l.free(); b->d_shell_K.free();
     b->d_shell_f0.free(); b->d_shell_poff.free(); b->d_shell_R.free(); b->d_shell_alpha.free();
     b->d_shell_coef.free(); b->d_fscale.free(); b->d_pair_a.free(); b->d_pair_b.free();
@@ -624,6 +631,7 @@ void mess_free_basis(mess_basis* b)
     b->bins.bra.free(); b->bins.kbeg.free(); b->bins.offs.free(); b->bins.seg.free();
     mess_free_jk_graphs(b);
     b->d_D32.free(); b->d_Ddf.free(); b->d_stage.free();
+    mess_free_xc(b);
     if (b->dconv_free) cudaEventDestroy(b->dconv_free);
     b->dconv_free = nullptr;
 }

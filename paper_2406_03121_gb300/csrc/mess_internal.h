@@ -96,6 +96,17 @@ struct JKGraph {
     mess_jk_info info{};
 };
 
+// Exchange-correlation quadrature of a basis (built on first use, kept with the basis): grid points
+// and weights (Becke-partitioned), and every basis function's value and gradient at its molecule's
+// points ([npts_m][n_m] blocks per molecule; gradients as three such blocks).
+struct XcState {
+    bool ready = false;
+    long long npts = 0, ao = 0, mol_npts_max = 0;
+    DevBuf<double> pts, w, phi, dphi, vrho, vgrad, Exc;
+    DevBuf<int> atom, mol, fbase, shell_off, shell_n, shell_fl;
+    DevBuf<long long> pbase, aobase;
+};
+
 // A basis of one molecule, or (internally) of a batch of molecules: shells, pairs and quartets
 // never couple two molecules, and every n x n matrix of a molecule m is the block
 // [mol_base[m], mol_base[m] + n_m^2) of a packed array (row-major, row stride n_m).
@@ -127,6 +138,7 @@ struct mess_basis {
     DevBuf<PrimPairRec<float>> d_pp32;
     DevBuf<int> d_pp_off, d_pp_n, d_fa, d_fb, d_same;
     DevBuf<double> d_AB, d_Q, d_Ccen;
+    DevBuf<float> d_Qf;            // Schwarz factor per pair in FP32 (density screening)
     DevBuf<float> d_ABf, d_Cf;
     DevBuf<double> d_boys64;
     DevBuf<float> d_boys32;
@@ -152,6 +164,7 @@ struct mess_basis {
     cudaEvent_t dconv_free = nullptr;
     std::vector<JKGraph> graphs;   // J/K graphs of repeated builds (at most 4, oldest dropped first)
     DevBuf<double> d_stage;        // D, J, K of the host-buffer J/K build (kept for repeated calls)
+    XcState xc;                    // exchange-correlation grid (Kohn-Sham functionals)
 };
 
 // one-electron integrals on the device (one_e.cu)
@@ -171,6 +184,12 @@ void mess_free_basis(mess_basis* b);
 mess_status mess_atoms_basis(const mess_basis* b, std::vector<int>& elements, mess_basis** out);
 // batched SCF on an internal batch basis, final densities into dD (device, packed) (scf.cu)
 mess_status mess_scf_batch_density(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* dD);
+// exchange-correlation (xc.cu): the grid and basis-function values of b (once), then for a packed
+// density dD the matrix dV (packed, overwritten) and E_xc per molecule (dExc, overwritten) of
+// functional kind 1 (LDA) or 2 (PBE); on stream s, no allocation after the first call
+mess_status mess_xc_prepare(mess_basis* b, cudaStream_t s);
+mess_status mess_xc_eval(mess_basis* b, int kind, const double* dD, double* dV, double* dExc, cudaStream_t s);
+void mess_free_xc(mess_basis* b);
 // learned guess: predicted D0 of every molecule of b (device, packed) (mlp.cu)
 mess_status mess_mlp_guess_device(const mess_mlp* m, const mess_basis* b, double* dD0, cudaStream_t s);
 // whether the quartet bins for these options are built (a J/K build with them would not allocate);
