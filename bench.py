@@ -320,18 +320,20 @@ def _scf_section(mess, args):
 
 def _mlp_section(mess, args):
     """Learned SCF guess: the MLP trained by the library's own kernels on converged densities of
-    seeded alkane conformers with n = 1..8 (seed 2004), then batched SCF of unseen conformers with
-    n = 9..12 (seed 2005) from the core-Hamiltonian, SAD and learned guesses (reduced precision);
-    iterations to convergence, wall time, and the spread of the final energies across guesses."""
+    seeded alkane conformers with n = 1..8 (seed 2004), then the SCF of unseen conformers with
+    n = 9..12 (seed 2005) from the core-Hamiltonian, SAD and learned guesses: the energy error after
+    one diagonalisation of the guess's Fock matrix (FP64, the SCF stopped after its second energy),
+    iterations to convergence and wall time of the batched reduced-precision SCF, and the spread of
+    the final energies across guesses."""
     import tempfile
     import mess_inputs as mi
     sto = mi.basis_path("sto-3g")
     train = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(args.mlp_molecules, 1, 8, 2004)]
-    test = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(64, 9, 12, 2005)]
+    test = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(args.mlp_test_molecules, 9, 12, 2005)]
     kw = dict(prec="mixed", split_df32=True)
     net = mess.MLP(seed=3)
     t0 = time.perf_counter()
-    losses = net.train(train, epochs=40, batch_rows=4096, lr=2e-3, **kw)
+    losses = net.train(train, epochs=40, batch_rows=8192, lr=2e-3, **kw)
     t_train = time.perf_counter() - t0
     out = {"workload": f"train: {len(train)} alkanes n = 1..8 (seed 2004, labels = converged densities of the "
                        f"library's own SCF); test: {len(test)} alkanes n = 9..12 (seed 2005); STO-3G",
@@ -347,8 +349,12 @@ def _mlp_section(mess, args):
             res, st = mess.scf_batch(test, guess=guess, **kw, **extra)
             dt = time.perf_counter() - t0
             energies[name] = [r["E_total"] for r in res]
+            first, _ = mess.scf_batch(test, guess=guess, prec="fp64", max_iter=2, **extra)
+            de1 = [f["E_total"] - r["E_total"] for f, r in zip(first, res)]
             out[name] = {"mean_iterations": sum(r["iterations"] for r in res) / len(res),
-                         "converged": sum(int(r["converged"]) for r in res), "molecules_per_s": len(res) / dt}
+                         "converged": sum(int(r["converged"]) for r in res), "molecules_per_s": len(res) / dt,
+                         "mean_dE_after_one_diagonalisation_Ha": sum(de1) / len(de1),
+                         "max_dE_after_one_diagonalisation_Ha": max(de1)}
     out["max_abs_dE_between_guesses_Ha"] = max(abs(a - b) for k in ("sad", "mlp")
                                                for a, b in zip(energies[k], energies["core"]))
     return out
@@ -622,8 +628,10 @@ def main():
                     help="alkane conformers of the batched-SCF section (0: skip it)")
     ap.add_argument("--scf-fp64-molecules", dest="scf_fp64_molecules", type=int, default=256,
                     help="molecules of that batch also run in plain FP64")
-    ap.add_argument("--mlp-molecules", dest="mlp_molecules", type=int, default=512,
+    ap.add_argument("--mlp-molecules", dest="mlp_molecules", type=int, default=20000,
                     help="training conformers of the learned-guess section (0: skip it)")
+    ap.add_argument("--mlp-test-molecules", dest="mlp_test_molecules", type=int, default=512,
+                    help="held-out conformers (n = 9..12) of the learned-guess section")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

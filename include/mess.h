@@ -210,6 +210,18 @@ mess_status mess_xc(const mess_basis* b, int xc, const double* D, double* Exc, d
  * MESS_ENOMEM, MESS_ECUDA, MESS_ENUMERIC (singular overlap, non-finite energy). */
 mess_status mess_scf(const mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* D_out);
 
+/* Nuclear gradient dE/dR of the closed-shell Hartree-Fock energy at the SCF solution (the paper
+ * differentiates E(P) + nuclear_energy automatically, Secs. 1 and 4; here the analytic expression):
+ * runs mess_scf with opts (prec as there; the derivative integrals are FP64), then
+ *   dE/dA_x = sum_{m on A, n} [2 D_mn (dm|h|n) + D_mn (2 J'_mn - K'_mn) - 2 W_mn (dm|n)]
+ *             - 2 sum_{m,n} D_mn (dm|V_A|n) + dE_nuc/dA_x,
+ * dm the derivative of basis function m with respect to its own centre, J'_mn = sum_ls (dm n|l s) D_ls,
+ * K'_mn = sum_ls (dm l|n s) D_ls, W = D F D / 2, V_A the attraction of nucleus A.  Single-molecule
+ * bases with shells up to p (STO-3G, 6-31G: the derivative of a d shell needs f functions), xc = 0.
+ * grad: natom x 3 doubles (hartree/bohr); res (nullable): the SCF result.  Errors: as mess_scf;
+ * MESS_ENOTIMPL (d shells, xc != 0). */
+mess_status mess_gradient(const mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* grad);
+
 /* Batched SCF over many molecules (the paper's vmap over conformers, Sec. 5.2): every molecule of
  * bases[0..nmol) (single-molecule bases, any sizes) in the same kernel launches - the J/K kernels
  * take quartets of all molecules from one set of bins; Fock, DIIS, Jacobi and the density run one

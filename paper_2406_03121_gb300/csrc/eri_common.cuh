@@ -539,12 +539,13 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
     const int b0 = P.pp_off[bp], b1 = b0 + (live ? P.pp_n[bp] : 0);
     const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
     const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);
+    // ket primitives outside (per-lane records read once), bra primitives inside (the same for the warp)
 #pragma unroll 1
-    for (int ib = b0; ib < b1; ++ib) {
-        const PrimPair<R> pb = P.load(ib);
+    for (int ik = k0; ik < (live ? k1 : k0); ++ik) {
+        const PrimPair<R> pk = P.load(ik);
 #pragma unroll 1
-        for (int ik = k0; ik < k1; ++ik) {
-            const PrimPair<R> pk = P.load(ik);
+        for (int ib = b0; ib < b1; ++ib) {
+            const PrimPair<R> pb = P.load(ib);
             R rz, srz;
             recip_and_sqrt(pb.zeta + pk.zeta, rz, srz);
             const R roz = pk.zeta * rz, roe = pb.zeta * rz, oo2ze = R(0.5) * rz;

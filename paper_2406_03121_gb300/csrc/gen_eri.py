@@ -621,12 +621,15 @@ def emit_class_straight(cls):
         for fi, f in enumerate(v.fs):
             body.append(f"            acc[{ei * len(v.fs) + fi}] += {v.names[(e, f, 0)]};")
     lines.append("    if constexpr (G == 1) {")
+    lines.append("    // ket primitives outside: each lane's ket records (different for every lane) are read once;")
+    lines.append("    // the bra records inside are the same for the whole warp (one broadcast load each)")
+    lines.append("    const int k1l = live ? k1 : k0;")
     lines.append("#pragma unroll 1")
-    lines.append("    for (int ib = b0; ib < b1; ++ib) {")
-    lines.append("        const PrimPair<R> pb = P.load(ib);")
+    lines.append("    for (int ik = k0; ik < k1l; ++ik) {")
+    lines.append("        const PrimPair<R> pk = P.load(ik);")
     lines.append(f"#pragma unroll ({'PrimUnroll<R>::value' if len(v.order) <= PRIM_UNROLL_MAX_VRR else 1})")
-    lines.append("        for (int ik = k0; ik < k1; ++ik) {")
-    lines.append("            const PrimPair<R> pk = P.load(ik);")
+    lines.append("        for (int ib = b0; ib < b1; ++ib) {")
+    lines.append("            const PrimPair<R> pb = P.load(ib);")
     lines += body
     lines.append("        }")
     lines.append("    }")

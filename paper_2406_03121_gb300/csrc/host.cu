@@ -659,6 +659,39 @@ extern "C" mess_status mess_basis_create(int natom, const int* Z, const double* 
     return MESS_OK;
 }
 
+mess_status mess_derivative_basis(const mess_basis* b, mess_basis** out, std::vector<int>& raised,
+                                  std::vector<int>& lowered)
+{
+    if (b->nmol != 1) { mess_set_error("derivative basis: single-molecule bases only"); return MESS_EINVAL; }
+    std::vector<HostShell> sh(b->shells.begin(), b->shells.end());
+    const int ns = (int)sh.size();
+    raised.assign(ns, -1);
+    lowered.assign(ns, -1);
+    for (int k = 0; k < ns; ++k) {
+        HostShell r = b->shells[k];
+        if (r.l + 1 > MESS_LMAX) { mess_set_error("derivative basis: shells up to l = %d", MESS_LMAX - 1); return MESS_EINVAL; }
+        r.l += 1;
+        for (int i = 0; i < r.K; ++i) r.coef[i] = 2.0 * r.alpha[i] * b->shells[k].coef[i];
+        raised[k] = (int)sh.size();
+        sh.push_back(r);
+    }
+    for (int k = 0; k < ns; ++k) {
+        if (b->shells[k].l == 0) continue;
+        HostShell r = b->shells[k];
+        r.l -= 1;
+        lowered[k] = (int)sh.size();
+        sh.push_back(r);
+    }
+    mess_basis* e = new (std::nothrow) mess_basis();
+    if (!e) { mess_set_error("host allocation failed"); return MESS_ENOMEM; }
+    add_molecule(e, b->Z, b->xyz, sh);
+    mess_status st = build_pairs(e);
+    if (st == MESS_OK) st = build_schwarz(e);
+    if (st != MESS_OK) { mess_free_basis(e); delete e; return st; }
+    *out = e;
+    return MESS_OK;
+}
+
 mess_status mess_atoms_basis(const mess_basis* b, std::vector<int>& elements, mess_basis** out)
 {
     elements.clear();

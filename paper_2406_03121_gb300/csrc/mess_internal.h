@@ -177,6 +177,12 @@ cudaError_t mess_launch_convert_density(const double* D, float* D32, float2* Ddf
 void mess_boys_table(std::vector<double>& tab);
 // bins (host.cu)
 mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split);
+// derivative basis (host.cu) of a single-molecule basis whose shells have l < MESS_LMAX: the shells of b
+// (same order, so its functions come first), then for every shell k a raised shell raised[k] (l + 1,
+// coefficients 2 alpha_i c_i) and for l > 0 a lowered shell lowered[k] (l - 1, coefficients c_i), -1 if
+// none; the derivative of a function of shell k with respect to its centre combines the two
+mess_status mess_derivative_basis(const mess_basis* b, mess_basis** out, std::vector<int>& raised,
+                                  std::vector<int>& lowered);
 // batches (host.cu): one basis over several molecules (copies of the given bases' shells)
 mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basis** out);
 void mess_free_basis(mess_basis* b);

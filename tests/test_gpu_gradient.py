@@ -1,0 +1,36 @@
+"""Analytic nuclear gradient of the Hartree-Fock energy on the GPU against the oracle's numerical
+derivative of its own SCF energy (hartree/bohr), on distorted geometries."""
+import numpy as np
+import pytest
+
+import mess_inputs as mi
+from oracle import gradient as og
+
+pytestmark = pytest.mark.gpu
+
+
+def _distorted(mol, seed, scale=0.1):
+    return mi.Molecule(mol.name + "_d", mol.Z, mol.xyz + np.random.default_rng(seed).normal(scale=scale, size=mol.xyz.shape))
+
+
+@pytest.mark.parametrize("name,mol,basis", [
+    ("h2o_sto3g", _distorted(mi.h2o(), 1), "sto-3g"),
+    ("h2o_631g", _distorted(mi.h2o(), 2), "6-31g"),
+    ("ch4_sto3g", _distorted(mi.alkane(1, np.random.default_rng(4)), 3), "sto-3g"),
+], ids=lambda x: x if isinstance(x, str) else "")
+def test_gradient_matches_the_oracle(mess, name, mol, basis):
+    path = mi.basis_path(basis)
+    g = mess.Basis.from_molecule(mol, path)
+    r, grad = g.gradient(prec="fp64", conv_E=1e-12, conv_comm=1e-10)
+    assert r["converged"] == 1
+    ref = og.fd_gradient(mol.Z, mol.xyz, path)
+    print(name, "max |dG| =", np.abs(grad - ref).max())
+    assert np.abs(grad - ref).max() <= 1e-6
+    assert np.abs(grad.sum(axis=0)).max() <= 1e-8
+
+
+def test_gradient_refuses_d_shells_and_functionals(mess):
+    g = mess.Basis.from_molecule(mi.h2o(), mi.basis_path("6-31gs"))
+    with pytest.raises(mess.MessError) as e:
+        g.gradient()
+    assert e.value.status == mess.MESS_ENOTIMPL
