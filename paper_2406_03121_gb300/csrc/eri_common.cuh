@@ -108,6 +108,7 @@ template <typename R> struct PairTable {
     // two shells of pair p.  Every density element a quartet's J/K terms read lies in one of those
     // rows, so each skipped contribution is below dtau (the incremental Fock builds of an SCF, whose
     // density changes shrink as it converges).
+    const KetRec* __restrict__ rec = nullptr;   // per pair (pair order)
     const float* __restrict__ Qf = nullptr;     // Schwarz factor per pair (FP32)
     const float* __restrict__ dmax = nullptr;
     float dtau = 0.f;
@@ -148,6 +149,66 @@ __device__ __forceinline__ df32 pair_ac(const PairTable<df32>& P, int bp, int kp
 __device__ __forceinline__ double pair_ab(const PairTable<double>& P, int p, int x) { return P.AB[3 * p + x]; }
 __device__ __forceinline__ df32 pair_ab(const PairTable<df32>& P, int p, int x) { return df32(P.AB[3 * p + x]); }
 __device__ __forceinline__ float pair_ab(const PairTable<float>& P, int p, int x) { return __ldg(P.ABf + 3 * p + x); }
+
+// The ket side of a quartet as the recursion needs it: its primitive range, A - C (bra first centre
+// minus ket first centre, formed as in pair_ac) and C - D, from the ket's record.
+template <typename R> struct KetView {
+    int k0, nk;
+    R AC[3], CD[3];
+};
+
+__device__ __forceinline__ int4 ket_hdr(const KetRec* r) { return __ldg(reinterpret_cast<const int4*>(r)); }
+
+__device__ __forceinline__ KetView<double> ket_view(const PairTable<double>& P, int bp, const KetRec* r, int4 h)
+{
+    KetView<double> v;
+    v.k0 = h.x;
+    v.nk = h.y;
+    const double2 c01 = __ldg(reinterpret_cast<const double2*>(r) + 1);
+    const double2 c2a0 = __ldg(reinterpret_cast<const double2*>(r) + 2);
+    const double2 a12 = __ldg(reinterpret_cast<const double2*>(r) + 3);
+    v.AC[0] = __ldg(P.C + 3 * bp) - c01.x;
+    v.AC[1] = __ldg(P.C + 3 * bp + 1) - c01.y;
+    v.AC[2] = __ldg(P.C + 3 * bp + 2) - c2a0.x;
+    v.CD[0] = c2a0.y; v.CD[1] = a12.x; v.CD[2] = a12.y;
+    return v;
+}
+__device__ __forceinline__ KetView<float> ket_view(const PairTable<float>& P, int bp, const KetRec* r, int4 h)
+{
+    KetView<float> v;
+    v.k0 = h.x;
+    v.nk = h.y;
+    const float4 f0 = __ldg(reinterpret_cast<const float4*>(r) + 4);   // Cf hi x y z, lo x
+    const float4 f1 = __ldg(reinterpret_cast<const float4*>(r) + 5);   // lo y z, ABf x y
+    const float4 f2 = __ldg(reinterpret_cast<const float4*>(r) + 6);   // ABf z, pair
+    const float* cb = P.Cf + 6 * bp;
+    v.AC[0] = (__ldg(cb) - f0.x) + (__ldg(cb + 3) - f0.w);
+    v.AC[1] = (__ldg(cb + 1) - f0.y) + (__ldg(cb + 4) - f1.x);
+    v.AC[2] = (__ldg(cb + 2) - f0.z) + (__ldg(cb + 5) - f1.y);
+    v.CD[0] = f1.z; v.CD[1] = f1.w; v.CD[2] = f2.x;
+    return v;
+}
+__device__ __forceinline__ KetView<df32> ket_view(const PairTable<df32>& P, int bp, const KetRec* r, int4 h)
+{
+    KetView<df32> v;
+    v.k0 = h.x;
+    v.nk = h.y;
+    const float4 f0 = __ldg(reinterpret_cast<const float4*>(r) + 4);
+    const float4 f1 = __ldg(reinterpret_cast<const float4*>(r) + 5);
+    const float* cb = P.Cf + 6 * bp;
+    const float kh[3] = {f0.x, f0.y, f0.z}, kl[3] = {f0.w, f1.x, f1.y};
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const df32 hi = df_two_sum(__ldg(cb + x), -kh[x]);
+        const df32 lo = df_two_sum(__ldg(cb + 3 + x), -kl[x]);
+        v.AC[x] = hi + lo;
+    }
+    const double2 c2a0 = __ldg(reinterpret_cast<const double2*>(r) + 2);
+    const double2 a12 = __ldg(reinterpret_cast<const double2*>(r) + 3);
+    v.CD[0] = df32(c2a0.y); v.CD[1] = df32(a12.x); v.CD[2] = df32(a12.y);
+    return v;
+}
+__device__ __forceinline__ int ket_pair(const KetRec* r) { return __ldg(&r->pair); }
 
 // ------------------------------------------------------------------------------------------
 // Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt, m = 0..L.
@@ -429,13 +490,16 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         const long long q = valid ? q0 : b.total - 1;                                               \
         const int i = find_bra(b, q);                                                  \
         const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));                            \
-        const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);                                     \
+        const int bp = __ldg(b.bra + i);                                                            \
+        const KetRec* kr = b.ketrec + j;                                                            \
+        const int4 kh = ket_hdr(kr);                                                                \
+        const int kp = ket_pair(kr);                                                                \
         /* quartets past the end or of a molecule that has left: no work; a warp without any    */ \
         /* quartet to do leaves (lanes of a group share the quartet, so groups leave together)  */ \
         const bool live = valid && P.live(bp) && P.dens_ok(bp, kp);                                 \
         if (__all_sync(0xffffffffu, !live)) return;                                                 \
         R I[(NA) * (NB) * (NC) * (ND)];                                                             \
-        eri_##TAG<R, BMODE, G>(P, bp, kp, g, I, live);                                              \
+        eri_##TAG<R, BMODE, G>(P, bp, ket_view(P, bp, kr, kh), g, I, live);                        \
         DigestCtx<R> c;                                                                              \
         {                                                                                           \
             const int m_ = __ldg(P.mol + bp);                                                       \
@@ -444,10 +508,10 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         }                                                                                           \
         (void)n;                                                                                    \
         c.fa = __ldg(P.fa + bp); c.fb = __ldg(P.fb + bp);                                           \
-        c.fc = __ldg(P.fa + kp); c.fd = __ldg(P.fb + kp);                                           \
+        c.fc = kh.z & 0xffff; c.fd = kh.z >> 16;                                                    \
         R s = live ? R(1) : R(0);                                                                   \
         if (__ldg(P.same + bp)) s *= R(0.5);                                                        \
-        if (__ldg(P.same + kp)) s *= R(0.5);                                                        \
+        if (kh.w & 1) s *= R(0.5);                                                                  \
         if (bp == kp) s *= R(0.5);                                                                  \
         if (G == 1) {                                                                               \
             c.warp_reduce_ab = warp_uniform_int(bp);                                                \
@@ -467,7 +531,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         const int j = b.kbeg[i] + (int)(q - b.offs[i]);                                             \
         const int bp = b.bra[i], kp = b.ket[j];                                                     \
         double I[(NA) * (NB) * (NC) * (ND)];                                                        \
-        eri_##TAG<double, 0, 1>(P, bp, kp, 0, I);                                                   \
+        eri_##TAG<double, 0, 1>(P, bp, ket_view(P, bp, P.rec + kp, ket_hdr(P.rec + kp)), 0, I);     \
         const int fa = P.fa[bp], fb = P.fb[bp], fc = P.fa[kp], fd = P.fb[kp];                       \
         const size_t nn = (size_t)n;                                                                \
         for (int ia = 0; ia < (NA); ++ia)                                                           \
@@ -497,7 +561,7 @@ __device__ __forceinline__ bool warp_uniform_int(int v)
         if (t >= npairs) return;                                                                    \
         const int p = pairs[t];                                                                     \
         double I[(NA) * (NB) * (NA) * (NB)];                                                        \
-        eri_##TAG<double, 0, 1>(P, p, p, 0, I);                                                     \
+        eri_##TAG<double, 0, 1>(P, p, ket_view(P, p, P.rec + p, ket_hdr(P.rec + p)), 0, I);         \
         double m = 0.0;                                                                             \
         for (int ia = 0; ia < (NA); ++ia)                                                           \
             for (int ib = 0; ib < (NB); ++ib)                                                       \
@@ -526,7 +590,7 @@ template <typename R> __device__ __forceinline__ R pick3(int d, R x, R y, R z)
 }
 
 template <typename R, int BMODE, int L, int NV, int NH, int NACC, int NVOPS, int NHOPS, int NINT>
-__device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int kp,
+__device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, const KetView<R>& kv,
                                             const uint4* __restrict__ vprog, const uint2* __restrict__ hprog,
                                             const int* __restrict__ fslot, const double* __restrict__ fscale,
                                             const float* __restrict__ fscale_hi, const float* __restrict__ fscale_lo,
@@ -537,8 +601,8 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
 #pragma unroll 1
     for (int k = 0; k < NACC; ++k) H[k] = R(0);
     const int b0 = P.pp_off[bp], b1 = b0 + (live ? P.pp_n[bp] : 0);
-    const int k0 = P.pp_off[kp], k1 = k0 + P.pp_n[kp];
-    const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);
+    const int k0 = kv.k0, k1 = k0 + kv.nk;
+    const R ACx = kv.AC[0], ACy = kv.AC[1], ACz = kv.AC[2];
     // ket primitives outside (per-lane records read once), bra primitives inside (the same for the warp)
 #pragma unroll 1
     for (int ik = k0; ik < (live ? k1 : k0); ++ik) {
@@ -587,7 +651,7 @@ __device__ __forceinline__ void eri_program(const PairTable<R>& P, int bp, int k
         }
     }
     const R ABx = pair_ab(P, bp, 0), ABy = pair_ab(P, bp, 1), ABz = pair_ab(P, bp, 2);
-    const R CDx = pair_ab(P, kp, 0), CDy = pair_ab(P, kp, 1), CDz = pair_ab(P, kp, 2);
+    const R CDx = kv.CD[0], CDy = kv.CD[1], CDz = kv.CD[2];
 #pragma unroll 1
     for (int o = 0; o < NHOPS; ++o) {
         const uint2 w = __ldg(hprog + o);
@@ -639,13 +703,17 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     R* Hp = Vp + NVI;
     const int i = find_bra(b, q);
     const int j = __ldg(b.kbeg + i) + (int)(q - __ldg(b.offs + i));
-    const int bp = __ldg(b.bra + i), kp = __ldg(b.ket + j);
+    const int bp = __ldg(b.bra + i);
+    const KetRec* kr = b.ketrec + j;
+    const int4 kh = ket_hdr(kr);
+    const int kp = ket_pair(kr);
     if (!P.live(bp) || !P.dens_ok(bp, kp)) return;   // the quartet's threads leave together
+    const KetView<R> kv = ket_view(P, bp, kr, kh);
     for (int k = plane; k < NACC; k += TP) Hp[k] = R(0);
     team_sync<TP>();
     const int b0 = P.pp_off[bp], nbp = P.pp_n[bp];
-    const int k0 = P.pp_off[kp], nkp = P.pp_n[kp];
-    const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);
+    const int k0 = kv.k0, nkp = kv.nk;
+    const R ACx = kv.AC[0], ACy = kv.AC[1], ACz = kv.AC[2];
 #pragma unroll 1
     for (int ip = PS ? pslot : 0; ip < nbp * nkp; ip += PS ? MESS_TEAM_WARPS : 1) {
         const int ib = b0 + ip / nkp, ik = k0 + ip % nkp;
@@ -706,7 +774,7 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
         __syncthreads();
     }
     const R ABx = pair_ab(P, bp, 0), ABy = pair_ab(P, bp, 1), ABz = pair_ab(P, bp, 2);
-    const R CDx = pair_ab(P, kp, 0), CDy = pair_ab(P, kp, 1), CDz = pair_ab(P, kp, 2);
+    const R CDx = kv.CD[0], CDy = kv.CD[1], CDz = kv.CD[2];
 #pragma unroll 1
     for (int lv = 0; lv < NHL; ++lv) {
         const int oend = __ldg(hlev + lv + 1);
@@ -724,9 +792,9 @@ __device__ __forceinline__ void jk_team_body(const BinLaunch& b, const PairTable
     const R* I = V;
     R s = R(1);
     if (__ldg(P.same + bp)) s *= R(0.5);
-    if (__ldg(P.same + kp)) s *= R(0.5);
+    if (kh.w & 1) s *= R(0.5);
     if (bp == kp) s *= R(0.5);
-    const int fa = __ldg(P.fa + bp), fb = __ldg(P.fb + bp), fc = __ldg(P.fa + kp), fd = __ldg(P.fb + kp);
+    const int fa = __ldg(P.fa + bp), fb = __ldg(P.fb + bp), fc = kh.z & 0xffff, fd = kh.z >> 16;
     const int mol_ = __ldg(P.mol + bp);
     const long long off_ = __ldg(P.mbase + mol_);
     D += off_;

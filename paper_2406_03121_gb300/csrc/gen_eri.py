@@ -588,15 +588,15 @@ def emit_class_straight(cls):
     lines = []
     lines.append(f"// ---- class ({la}{lb}|{lc}{ld}): {len(v.order)} VRR entries, {nacc} contracted, {nint} integrals")
     lines.append(f"template <typename R, int BMODE, int G>")
-    lines.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I, bool live = true)")
+    lines.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, const KetView<R>& kv, int g, R* I, bool live = true)")
     lines.append("{")
     lines.append(f"    R acc[{nacc}];")
     lines.append(f"#pragma unroll")
     lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = R(0);")
     lines.append("    const int b0 = P.pp_off[bp], b1 = b0 + (live ? P.pp_n[bp] : 0);   // !live: no primitive work")
-    lines.append("    const int k0 = P.pp_off[kp], nk = P.pp_n[kp], k1 = k0 + nk;")
+    lines.append("    const int k0 = kv.k0, nk = kv.nk, k1 = k0 + nk;")
     lines.append("    // A - C in FP64, then P - Q = (P - A) - (Q - C) + (A - C): no absolute coordinates in R")
-    lines.append("    const R ACx = pair_ac(P, bp, kp, 0), ACy = pair_ac(P, bp, kp, 1), ACz = pair_ac(P, bp, kp, 2);")
+    lines.append("    const R ACx = kv.AC[0], ACy = kv.AC[1], ACz = kv.AC[2];")
     body = []
     body.append("            R rz, srz;")
     body.append("            recip_and_sqrt(pb.zeta + pk.zeta, rz, srz);")
@@ -651,7 +651,7 @@ def emit_class_straight(cls):
     lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = group_sum<G>(acc[k]);")
     lines.append("    }")
     lines.append("    const R ABx = pair_ab(P, bp, 0), ABy = pair_ab(P, bp, 1), ABz = pair_ab(P, bp, 2);")
-    lines.append("    const R CDx = pair_ab(P, kp, 0), CDy = pair_ab(P, kp, 1), CDz = pair_ab(P, kp, 2);")
+    lines.append("    const R CDx = kv.CD[0], CDy = kv.CD[1], CDz = kv.CD[2];")
     lines.append("    (void)ABx; (void)ABy; (void)ABz; (void)CDx; (void)CDy; (void)CDz;")
     hb, hbf = hrr_bra(la, lb, v.fs, v.es, lines, "    ", "acc")
     hk, hkf = hrr_ket(lc, ld, v.fs, hb, la, lb, lines, "    ")
@@ -703,12 +703,12 @@ def emit_class(cls):
     L.append(f"__device__ const float fscaleh_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(h) + "f" for h in his) + "};")
     L.append(f"__device__ const float fscalel_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(l) + "f" for l in los) + "};")
     L.append("template <typename R, int BMODE, int G>")
-    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, int kp, int g, R* I, bool live = true)")
+    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, const KetView<R>& kv, int g, R* I, bool live = true)")
     L.append("{")
     L.append("    static_assert(G == 1, \"op-program classes run one thread per quartet\");")
     L.append("    (void)g;")
     L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
-             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kp, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, "
+             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kv, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, "
              f"fscaleh_{t}, fscalel_{t}, I, live);")
     L.append("}")
     return "\n".join(L) + "\n", info

@@ -335,6 +335,7 @@ static BinLaunch bin_launch(const mess_basis* b, const BinPart& p)
     L.offs = b->bins.offs.p + p.offs_off;
     L.seg = b->bins.seg.p + p.seg_off;
     L.ket = b->d_class_list[p.ket_list].p;
+    L.ketrec = b->d_ketrec[p.ket_list].p;
     L.nbra = p.nbra;
     L.total = p.total;
     return L;
@@ -489,6 +490,24 @@ static mess_status build_pairs(mess_basis* b)
     MESS_CUDA_TRY(b->d_fa.upload(fa));
     MESS_CUDA_TRY(b->d_fb.upload(fb));
     MESS_CUDA_TRY(b->d_same.upload(same));
+    // the per-pair records the J/K kernels read for the ket of a quartet
+    b->pair_rec.assign(b->npair, KetRec{});
+    for (int p = 0; p < b->npair; ++p) {
+        KetRec& r = b->pair_rec[p];
+        r.pp_off = b->pp_off[p];
+        r.pp_n = b->pp_n[p];
+        r.fab = fa[p] | (fb[p] << 16);
+        r.flags = same[p] | (b->pair_mol[p] << 1);
+        for (int x = 0; x < 3; ++x) {
+            r.C[x] = Ccen[3 * p + x];
+            r.AB[x] = AB[3 * p + x];
+            r.Cf[x] = Cf[6 * p + x];
+            r.Cf[3 + x] = Cf[6 * p + 3 + x];
+            r.ABf[x] = ABf[3 * p + x];
+        }
+        r.pair = p;
+    }
+    MESS_CUDA_TRY(b->d_pair_rec.upload(b->pair_rec));
     std::vector<double> tab;
     mess_boys_table(tab);
     MESS_CUDA_TRY(b->d_boys64.upload(tab));
@@ -528,6 +547,7 @@ static mess_status build_pairs(mess_basis* b)
     b->P64.Cf = b->P32.Cf = b->d_Cf.p;
     b->P64.ABf = b->P32.ABf = b->d_ABf.p;
     b->P64.mol = b->P32.mol = b->d_pair_mol.p;
+    b->P64.rec = b->P32.rec = b->Pdf.rec = b->d_pair_rec.p;
     b->P64.mbase = b->P32.mbase = b->d_mol_base.p;
     b->P64.mn = b->P32.mn = b->d_mol_n.p;
     b->P64.boys64 = b->P32.boys64 = b->d_boys64.p;
@@ -613,6 +633,9 @@ static mess_status build_schwarz(mess_basis* b)
             b->class_list[L] = l;
             b->class_seg[L] = seg;
             MESS_CUDA_TRY(b->d_class_list[L].upload(l));
+            std::vector<KetRec> rl(l.size());
+            for (size_t k = 0; k < l.size(); ++k) rl[k] = b->pair_rec[l[k]];
+            MESS_CUDA_TRY(b->d_ketrec[L].upload(rl));
         }
     }
     return MESS_OK;
@@ -628,6 +651,8 @@ void mess_free_basis(mess_basis* b)
     b->d_pair_mol.free(); b->d_mol_n.free(); b->d_mol_atom_off.free(); b->d_mol_atom_n.free();
     b->d_f_local.free(); b->d_mol_base.free();
     for (auto& d : b->d_class_list) d.free();
+    for (auto& d : b->d_ketrec) d.free();
+    b->d_pair_rec.free();
     b->bins.bra.free(); b->bins.kbeg.free(); b->bins.offs.free(); b->bins.seg.free();
     mess_free_jk_graphs(b);
     b->d_D32.free(); b->d_Ddf.free(); b->d_stage.free();

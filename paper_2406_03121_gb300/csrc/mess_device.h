@@ -21,10 +21,24 @@
 // One primitive pair: zeta, Px, Py, Pz, PAx, PAy, PAz, K, 1/(2 zeta) (+ padding to 16 bytes).
 template <typename R> struct alignas(16) PrimPairRec { R v[12]; };
 
+// Everything a J/K kernel reads about the ket pair of a quartet, in one 112-byte record (seven 16-byte
+// loads at most; the arithmetic reads only the ones it needs).  Stored per pair (pair order) and per
+// class list (list order, so that the consecutive kets of consecutive lanes are adjacent).
+//   [0]   pp_off, pp_n, fa | fb << 16 (first functions within the molecule), same | mol << 1
+//   [16]  C (centre of the pair's first shell) and A - B, FP64
+//   [64]  C as FP32 hi[3], lo[3]; A - B in FP32; the pair id
+struct alignas(16) KetRec {
+    int pp_off, pp_n, fab, flags;
+    double C[3], AB[3];
+    float Cf[6], ABf[3];
+    int pair;
+};
+
 // One launch over a class bin (a contiguous range of quartets of one angular class).
 struct BinLaunch {
     const int* bra;          // [nbra] pair ids, Q descending
     const int* ket;          // ket list (pair ids, Q descending)
+    const KetRec* ketrec;    // the ket list's records, same order
     const long long* offs;   // [nbra + 1] exclusive prefix of ket counts
     const int* kbeg;         // [nbra] first ket index of each bra
     const int* seg;          // [ceil(total / 32)] bra of quartet 32 k (narrows the bra search)

@@ -133,6 +133,9 @@ struct mess_basis {
     std::vector<int> class_list[MESS_NUM_PCLASS * MESS_NGROUP];
     std::vector<int> class_seg[MESS_NUM_PCLASS * MESS_NGROUP];
     DevBuf<int> d_class_list[MESS_NUM_PCLASS * MESS_NGROUP];
+    DevBuf<KetRec> d_ketrec[MESS_NUM_PCLASS * MESS_NGROUP];   // the lists' pair records, list order
+    std::vector<KetRec> pair_rec;                             // per pair
+    DevBuf<KetRec> d_pair_rec;
 
     DevBuf<PrimPairRec<double>> d_pp64;
     DevBuf<PrimPairRec<float>> d_pp32;

@@ -53,29 +53,33 @@ def test_loss_and_gradient_match_oracle(mess, propane):
 
 
 def test_training_gains_over_the_plain_guesses(mess, tmp_path):
-    train = mi.alkane_batch(48, 1, 4, 2004)
-    test = mi.alkane_batch(4, 5, 6, 2005)
-    bases = [mess.Basis.from_molecule(m, mi.basis_path("sto-3g")) for m in train]
+    """Trained on converged densities of small alkanes (n = 1..6), the learned guess is checked on
+    unseen longer ones (n = 7..8): its energy error after one diagonalisation of its Fock matrix must
+    be below that of the SAD guess (and far below the core-Hamiltonian guess's), it must converge in
+    fewer iterations than the core-Hamiltonian guess, and every guess reaches the same energy."""
+    sto = mi.basis_path("sto-3g")
+    train = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(400, 1, 6, 2004)]
+    test = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(16, 7, 8, 2005)]
     net = mess.MLP(seed=3)
-    losses = net.train(bases, epochs=40, batch_rows=512, lr=2e-3, prec="fp64")
+    losses = net.train(train, epochs=40, batch_rows=4096, lr=2e-3, prec="mixed", split_df32=True)
     assert losses[-1] < 0.25 * losses[0]
     w = str(tmp_path / "guess.bin")
     net.save(w)
-    its = {"core": [], "sad": [], "mlp": []}
-    for m in test:
-        b = mess.Basis.from_molecule(m, mi.basis_path("sto-3g"))
-        rc = b.scf(guess=mess.MESS_GUESS_CORE)
-        rs = b.scf(guess=mess.MESS_GUESS_SAD)
-        rm = b.scf(guess=mess.MESS_GUESS_MLP, mlp_weights=w)
-        for r in (rc, rs, rm):
-            assert r["converged"] == 1
-        assert abs(rm["E_total"] - rc["E_total"]) < 1e-8 and abs(rs["E_total"] - rc["E_total"]) < 1e-8
-        its["core"].append(rc["iterations"])
-        its["sad"].append(rs["iterations"])
-        its["mlp"].append(rm["iterations"])
-    print("mean SCF iterations", {k: float(np.mean(v)) for k, v in its.items()})
-    assert np.mean(its["mlp"]) < np.mean(its["core"])
-    assert np.mean(its["sad"]) < np.mean(its["core"])
+    guesses = {"core": dict(guess=mess.MESS_GUESS_CORE), "sad": dict(guess=mess.MESS_GUESS_SAD),
+               "mlp": dict(guess=mess.MESS_GUESS_MLP, mlp_weights=w)}
+    final, its, de1 = {}, {}, {}
+    for name, kw in guesses.items():
+        res, st = mess.scf_batch(test, prec="fp64", **kw)
+        assert st == mess.MESS_OK
+        first, _ = mess.scf_batch(test, prec="fp64", max_iter=2, **kw)
+        final[name] = np.array([r["E_total"] for r in res])
+        its[name] = float(np.mean([r["iterations"] for r in res]))
+        de1[name] = float(np.mean([f["E_total"] - r["E_total"] for f, r in zip(first, res)]))
+    print("mean SCF iterations", its, "mean energy error after one diagonalisation", de1)
+    for name in ("sad", "mlp"):
+        assert np.abs(final[name] - final["core"]).max() < 1e-8
+    assert de1["mlp"] < de1["sad"] < de1["core"]
+    assert its["mlp"] < its["core"]
 
 
 def test_mlp_guess_rejects_non_minimal_basis(mess, tmp_path):
