@@ -241,18 +241,19 @@ def _oracle_full_h2o():
     return out
 
 
+JK_KERNEL_SOURCES = ("gen_eri.py", "eri_common.cuh", "eri_launch.h", "mess_device.h", "df32.cuh")
+
+
 def _source_digest():
-    """Digest of the library's kernel and host sources (the counters of a profile taken with other
-    sources no longer describe these kernels)."""
+    """Digest of the sources the J/K kernels are generated and compiled from (the counters of a
+    profile taken with other kernel sources no longer describe these kernels)."""
     import hashlib
     h = hashlib.sha256()
-    pkg = os.path.join(ROOT, "paper_2406_03121_gb300")
-    for d in (os.path.join(pkg, "csrc"), os.path.join(ROOT, "include")):
-        for f in sorted(os.listdir(d)):
-            if f.endswith((".cu", ".cuh", ".h", ".py")):
-                h.update(f.encode())
-                with open(os.path.join(d, f), "rb") as fh:
-                    h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2406_03121_gb300", "csrc")
+    for f in JK_KERNEL_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -118,7 +118,9 @@ typedef struct {
 /* Build the contracted Cartesian basis of a structure (paper Sec. 3 LCAO basis; Sec. 5.1 basisset)
  * from a basis data file: "element <sym>" lines followed by shells "<S|P|D|SP> <nprim>" and nprim
  * lines "exponent coefficient(s)".  Computes on the GPU the primitive-pair tables (Gaussian product
- * theorem) and the Schwarz factors Q_ab = sqrt(max |(mn|mn)|) of every shell pair.
+ * theorem) and the Schwarz factors Q_ab = sqrt(max |(mn|mn)|) of every shell pair - on the first call
+ * that computes on this basis alone (a basis used only inside batches never builds its own), so CUDA
+ * errors of that step are reported by that call.
  * Z: natom ints; xyz_bohr: natom*3 doubles.  *out receives a new basis (free with mess_basis_destroy).
  * Errors: MESS_EINVAL (unknown element, unreadable or malformed file, natom <= 0), MESS_ENOMEM,
  * MESS_ECUDA. */
@@ -200,9 +202,10 @@ mess_status mess_xc(const mess_basis* b, int xc, const double* D, double* Exc, d
  * mess_jk_build_device with opts->prec / schwarz_tau / fp64_tau, F = H + J - K/2, DIIS, the
  * diagonalisation of X^T F X (one thread block per molecule, cyclic Jacobi, FP64) and D = 2 C_occ C_occ^T.
  * With prec MESS_MIXED / MESS_FP32 the iterations use the reduced-precision builds and the reported
- * energy is that of the final density with one build in which every quartet runs in double-float
- * (split_df32) or FP64: the integrals' rounding leaves the energy, and the density's residual
- * error enters it only at second order.
+ * energy E_total is that of the final density from one full build in which the quartets above a ten
+ * times lower split threshold (MESS_MIXED; every quartet for MESS_FP32) run in double-float
+ * (split_df32) or FP64: most of the integrals' rounding leaves the energy, and the density's residual
+ * error enters it only at second order.  E_iter is the iterations' own energy.
  * With opts->xc = 1 or 2 it is the Kohn-Sham SCF of that functional: F = H + J + V_xc and E_elec =
  * tr(D H) + 1/2 tr(D J) + E_xc (the exchange matrix K is not used).
  * D_out (nullable): host n*n final density.  Errors: MESS_ENOCONV (res holds the last iterate),

@@ -677,10 +677,28 @@ extern "C" mess_status mess_basis_create(int natom, const int* Z, const double* 
     mess_basis* b = new (std::nothrow) mess_basis();
     if (!b) { mess_set_error("host allocation failed"); return MESS_ENOMEM; }
     add_molecule(b, std::vector<int>(Z, Z + natom), std::vector<double>(xyz_bohr, xyz_bohr + 3 * natom), shells);
-    st = build_pairs(b);
-    if (st == MESS_OK) st = build_schwarz(b);
-    if (st != MESS_OK) { mess_free_basis(b); delete b; return st; }
     *out = b;
+    return MESS_OK;
+}
+
+mess_status mess_basis_gpu(mess_basis* b)
+{
+    if (!b) { mess_set_error("basis is NULL"); return MESS_EINVAL; }
+    if (b->gpu_ready) return MESS_OK;
+    mess_status st = build_pairs(b);
+    if (st == MESS_OK) st = build_schwarz(b);
+    if (st != MESS_OK) {
+        // leave the basis as created (host data only) so that a later call can try again
+        mess_free_basis(b);
+        b->npair = 0;
+        b->pair_a.clear(); b->pair_b.clear(); b->pair_class.clear(); b->pp_off.clear(); b->pp_n.clear();
+        b->pair_mol.clear(); b->Q.clear(); b->fscale.clear(); b->f_local.clear(); b->pair_rec.clear();
+        for (auto& l : b->class_list) l.clear();
+        for (auto& l : b->class_seg) l.clear();
+        b->P64 = PairTable<double>{}; b->P32 = PairTable<float>{}; b->Pdf = PairTable<df32>{};
+        return st;
+    }
+    b->gpu_ready = true;
     return MESS_OK;
 }
 
@@ -713,6 +731,7 @@ mess_status mess_derivative_basis(const mess_basis* b, mess_basis** out, std::ve
     mess_status st = build_pairs(e);
     if (st == MESS_OK) st = build_schwarz(e);
     if (st != MESS_OK) { mess_free_basis(e); delete e; return st; }
+    e->gpu_ready = true;
     *out = e;
     return MESS_OK;
 }
@@ -739,6 +758,7 @@ mess_status mess_atoms_basis(const mess_basis* b, std::vector<int>& elements, me
     mess_status st = build_pairs(a);
     if (st == MESS_OK) st = build_schwarz(a);
     if (st != MESS_OK) { mess_free_basis(a); delete a; return st; }
+    a->gpu_ready = true;
     *out = a;
     return MESS_OK;
 }
@@ -756,6 +776,7 @@ mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basi
     mess_status st = build_pairs(b);
     if (st == MESS_OK) st = build_schwarz(b);
     if (st != MESS_OK) { mess_free_basis(b); delete b; return st; }
+    b->gpu_ready = true;
     *out = b;
     return MESS_OK;
 }
@@ -787,6 +808,7 @@ extern "C" double mess_nuclear_repulsion(const mess_basis* b)
 extern "C" mess_status mess_schwarz(const mess_basis* b, double* Q)
 {
     if (!b || !Q) { mess_set_error("null argument"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     const int ns = (int)b->shells.size();
     for (int i = 0; i < ns * ns; ++i) Q[i] = 0.0;
     for (int p = 0; p < b->npair; ++p) {
@@ -800,6 +822,7 @@ extern "C" mess_status mess_schwarz(const mess_basis* b, double* Q)
 extern "C" mess_status mess_one_e_device(const mess_basis* b, double* dS, double* dT, double* dV, void* stream)
 {
     if (!b) { mess_set_error("basis is NULL"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     MESS_CUDA_TRY(mess_launch_one_e(b, dS, dT, dV, (cudaStream_t)stream));
     return MESS_OK;
 }
@@ -807,6 +830,7 @@ extern "C" mess_status mess_one_e_device(const mess_basis* b, double* dS, double
 static mess_status one_e_host(const mess_basis* b, double* S, double* T, double* V)
 {
     if (!b) { mess_set_error("basis is NULL"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     const size_t nn = (size_t)b->nbf * b->nbf;
     DevBuf<double> d;
     MESS_CUDA_TRY(d.alloc(nn));
@@ -994,6 +1018,7 @@ static mess_status jk_prepare(mess_basis* b, const double* dD, double* dJ, doubl
 {
     if (!b || !dD || !dJ || !dK) { mess_set_error("null argument"); return MESS_EINVAL; }
     if (dD == dJ || dD == dK || dJ == dK) { mess_set_error("D, J and K must be distinct buffers"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     double tau64 = 0.0;
     int split = 0;
     mess_status st = jk_options(opts, out, &tau64, &split);
@@ -1387,6 +1412,7 @@ extern "C" mess_status mess_jk_autotune(const mess_basis* bc, const double* D, c
 {
     if (!bc || !D) { mess_set_error("null argument"); return MESS_EINVAL; }
     mess_basis* b = const_cast<mess_basis*>(bc);
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     if (b->nmol != 1) { mess_set_error("mess_jk_autotune: single-molecule bases only"); return MESS_EINVAL; }
     const size_t nn = (size_t)b->nbf * b->nbf;
     DevBuf<double> d;
@@ -1411,6 +1437,7 @@ extern "C" mess_status mess_jk_build(const mess_basis* bc, const double* D, doub
 {
     if (!bc || !D || !J || !K) { mess_set_error("null argument"); return MESS_EINVAL; }
     mess_basis* b = const_cast<mess_basis*>(bc);
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     const size_t nn = (size_t)b->nbf * b->nbf;
     // D, J, K staged in a device buffer kept with the basis (allocated by the first call): repeated
     // calls allocate nothing, and their builds replay as one CUDA graph
@@ -1440,6 +1467,7 @@ extern "C" mess_status mess_eri_tensor(const mess_basis* bc, double* G)
 {
     mess_basis* b = const_cast<mess_basis*>(bc);
     if (!b || !G) { mess_set_error("null argument"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     const int n = b->nbf;
     if (n > 64) { mess_set_error("mess_eri_tensor: n = %d > 64", n); return MESS_EINVAL; }
     mess_status st = mess_ensure_bins(b, 0.0, 0.0, 0);

@@ -168,7 +168,12 @@ struct mess_basis {
     std::vector<JKGraph> graphs;   // J/K graphs of repeated builds (at most 4, oldest dropped first)
     DevBuf<double> d_stage;        // D, J, K of the host-buffer J/K build (kept for repeated calls)
     XcState xc;                    // exchange-correlation grid (Kohn-Sham functionals)
+    bool gpu_ready = false;        // pair tables and Schwarz factors built (on first use of the basis)
 };
+
+// the basis's device data (primitive-pair tables, records, Schwarz factors, class lists), built on
+// the first call that needs them; a basis used only inside batches never builds its own (host.cu)
+mess_status mess_basis_gpu(mess_basis* b);
 
 // one-electron integrals on the device (one_e.cu)
 cudaError_t mess_launch_one_e(const mess_basis* b, double* dS, double* dT, double* dV, cudaStream_t s);

@@ -686,6 +686,7 @@ extern "C" mess_status mess_mlp_features(const mess_basis* b, const double* D, f
 {
     if (!b || !nrows) { mess_set_error("null argument"); return MESS_EINVAL; }
     if (b->nmol != 1) { mess_set_error("single-molecule bases only"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     AtomTables t;
     mess_status st = atom_tables(b, t);
     if (st != MESS_OK) return st;
@@ -807,6 +808,7 @@ extern "C" mess_status mess_mlp_predict(const mess_mlp* m, const mess_basis* b, 
 {
     if (!m || !b || !D0) { mess_set_error("null argument"); return MESS_EINVAL; }
     if (b->nmol != 1) { mess_set_error("single-molecule bases only"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(const_cast<mess_basis*>(b)); if (gs != MESS_OK) return gs; }
     DevBuf<double> d;
     MESS_CUDA_TRY(d.alloc(b->packed));
     mess_status st = mess_mlp_guess_device(m, b, d.p, 0);

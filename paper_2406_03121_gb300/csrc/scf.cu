@@ -992,9 +992,10 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         }
     }
     if (o.prec != MESS_FP64 && !occ_in) {
-        // Reported energy of the reduced-precision forms: E at the final density with one Fock build
-        // in which every quartet runs in FP64-class arithmetic (double-float if split_df32, else
-        // FP64).  The integrals' rounding then no longer enters the energy, and the density's own
+        // Reported energy of the reduced-precision forms: E at the final density from one full Fock
+        // build in which the quartets above a ten times lower split threshold (MESS_MIXED; every
+        // quartet for MESS_FP32) run in FP64-class arithmetic (double-float if split_df32, else
+        // FP64).  Most of the integrals' rounding then leaves the energy, and the density's own
         // deviation from the FP64 solution enters it only at second order (E is stationary there).
         screen_reset.off();            // the energy's build: Schwarz screening only, every molecule
         for (int m = 0; m < b->nmol; ++m) { act[m] = 1; b->active[m] = 1; }
@@ -1002,7 +1003,9 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         MESS_CUDA_TRY(cudaMemcpyAsync(st.active.p, act.data(), b->nmol, cudaMemcpyHostToDevice, st.s));
         mess_jk_opts jf = jo;
         jf.prec = MESS_MIXED;
-        jf.fp64_tau = 1e-300;          // every quartet above the split threshold
+        // ten times more of the largest quartets in FP64-class arithmetic than in the iterations
+        const double it_tau = o.prec == MESS_MIXED ? (o.fp64_tau > 0.0 ? o.fp64_tau : MESS_DEFAULT_FP64_TAU) : 0.0;
+        jf.fp64_tau = it_tau > 0.0 ? 0.1 * it_tau : 1e-300;
         mess_status js = mess_jk_packed(b, st.D.p, st.Jt.p, st.Kt.p, &jf, nullptr);
         if (js != MESS_OK) return js;
         js = fock_energy();
@@ -1332,6 +1335,7 @@ extern "C" mess_status mess_scf(const mess_basis* bc, const mess_scf_opts* opts,
 {
     mess_basis* b = const_cast<mess_basis*>(bc);
     if (!b || !res) { mess_set_error("null argument"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(b); if (gs != MESS_OK) return gs; }
     return scf_run(b, opts, res, D_out, false);
 }
 
@@ -1352,6 +1356,7 @@ extern "C" mess_status mess_minimise(const mess_basis* bc, const mess_min_opts* 
 {
     mess_basis* b = const_cast<mess_basis*>(bc);
     if (!b || !res) { mess_set_error("null argument"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(b); if (gs != MESS_OK) return gs; }
     return min_run(b, opts, res, trace);
 }
 

@@ -463,6 +463,7 @@ extern "C" mess_status mess_xc(const mess_basis* bc, int xc, const double* D, do
     mess_basis* b = const_cast<mess_basis*>(bc);
     if (!b || !D) { mess_set_error("null argument"); return MESS_EINVAL; }
     if (xc != 1 && xc != 2) { mess_set_error("mess_xc: functional must be 1 (LDA) or 2 (PBE)"); return MESS_EINVAL; }
+    { const mess_status gs = mess_basis_gpu(b); if (gs != MESS_OK) return gs; }
     mess_status st = mess_xc_prepare(b, 0);
     if (st != MESS_OK) return st;
     const size_t nn = (size_t)b->packed;
