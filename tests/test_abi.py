@@ -43,3 +43,19 @@ def test_invalid_arguments_are_rejected_without_a_gpu(mess):
     assert b"bad structure" in m.mess_last_error()
     assert m.mess_basis_nbf(None) == -1
     m.mess_basis_destroy(None)
+
+
+def test_basis_creation_needs_no_gpu(mess):
+    """Creating a basis reads the basis file and expands the shells on the host only (the device
+    data is built by the first computation), so its sizes are available without a GPU."""
+    import mess_inputs as mi
+    g = mess.Basis.from_molecule(mi.h2o(), mi.basis_path("6-31gs"))
+    assert (g.nbf, g.nshell, g.nelectron) == (19, 10, 10)     # O: 1s 2s 2p 3s 3p d = 15; H: 2 x 2
+    # O-H 1.809 bohr twice, H-H 2 x 1.809 sin(52.26 deg)
+    import math
+    e = 2 * 8.0 / 1.809 + 1.0 / (2 * 1.809 * math.sin(math.radians(52.26)))
+    assert abs(g.nuclear_repulsion() - e) < 1e-12 * e
+    a = mess.Basis.from_molecule(mi.alkane(3, __import__("numpy").random.default_rng(1)), mi.basis_path("sto-3g"))
+    assert a.nbf == 7 * 3 + 2 and a.nelectron == 26
+    g.close()
+    a.close()
