@@ -242,3 +242,40 @@ def test_program_slots_in_bounds(cls):
             assert max(t, s1, s2) < nh
         assert all(f < nh for f, _ in prog["fin"])
         assert len(prog["fin"]) <= nv or not nvi
+
+
+@pytest.mark.parametrize("cls", CLASSES, ids=[GEN.tag(c) for c in CLASSES])
+def test_programs_read_only_written_slots(cls):
+    """In program order (one thread per quartet) and level by level (warp/block kernels), every slot
+    an op reads holds a value written earlier - H's first NACC slots hold the contracted values from
+    the start - so no kernel reads an indeterminate local or shared value (undefined behaviour that a
+    compiler may exploit)."""
+    for prog, team in ((GEN.build_program(cls), False), (GEN.build_team_program(cls), True)):
+        vw, hw = set(), set(range(prog["nacc"]))
+        def vrr(op):
+            kind, t, s1, s2, s3, s4, s5, d, m1, m2 = op
+            if kind == 0:
+                return [], ("V", t)
+            if kind == 3:
+                return [("V", t)], ("H", s1)
+            reads = [s1, s2] + ([s3, s4] if m1 else []) + ([s5] if (kind == 2 and m2) else [])
+            return [("V", x) for x in reads], ("V", t)
+        groups = ([prog["vrr"][a:b] for a, b in zip(prog["vlev"][:-1], prog["vlev"][1:])] if team
+                  else [[op] for op in prog["vrr"]])
+        for ops in groups:
+            writes = []
+            for op in ops:
+                reads, w = vrr(op)
+                for arr, x in reads:
+                    assert x in (vw if arr == "V" else hw), (GEN.tag(cls), "VRR reads", arr, x)
+                writes.append(w)
+            for arr, x in writes:
+                (vw if arr == "V" else hw).add(x)
+        hgroups = ([prog["hrr"][a:b] for a, b in zip(prog["hlev"][:-1], prog["hlev"][1:])] if team
+                   else [[op] for op in prog["hrr"]])
+        for ops in hgroups:
+            for (t, s1, s2, d, side) in ops:
+                assert s1 in hw and s2 in hw, (GEN.tag(cls), "HRR reads", s1, s2)
+            for (t, s1, s2, d, side) in ops:
+                hw.add(t)
+        assert all(f in hw for f, _ in prog["fin"])
