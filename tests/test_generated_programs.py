@@ -279,3 +279,18 @@ def test_programs_read_only_written_slots(cls):
             for (t, s1, s2, d, side) in ops:
                 hw.add(t)
         assert all(f in hw for f, _ in prog["fin"])
+
+
+@pytest.mark.parametrize("cls", CLASSES, ids=[GEN.tag(c) for c in CLASSES])
+def test_program_classes_stage_no_density_in_local_arrays(cls):
+    """The op-program classes digest with the density read through the read-only cache, never staged
+    in local arrays: a one-thread kernel that inlines the interpreter and also stages the density
+    blocks in local arrays was built with a stack frame smaller than its live arrays, and its
+    integrals came out as density values (the same source with the interpreter not inlined was
+    exact).  Straight-line classes stage the blocks, which then live in registers."""
+    _, info = GEN.emit_class(cls)
+    text = GEN.emit_digest(cls, unroll=(info["mode"] == "straight"))
+    staged = any(f"R {nm}[" in text for nm in ("Dab", "Dcd", "Dac", "Dad", "Dbc", "Dbd"))
+    assert staged == (info["mode"] == "straight"), (GEN.tag(cls), info["mode"])
+    src = open(os.path.join(ROOT, "paper_2406_03121_gb300", "csrc", "gen_eri.py")).read()
+    assert "emit_digest(cls, unroll=(info['mode'] == 'straight'))" in src
