@@ -200,7 +200,9 @@ mess_status mess_xc(const mess_basis* b, int xc, const double* D, double* Exc, d
  * guess, Pulay DIIS on FDS - SDF, converged when |dE| < conv_E and max|FDS - SDF| < conv_comm.
  * Runs entirely on the GPU: one-electron integrals, Loewdin X (Jacobi eigensolver), the J/K builds of
  * mess_jk_build_device with opts->prec / schwarz_tau / fp64_tau, F = H + J - K/2, DIIS, the
- * diagonalisation of X^T F X (one thread block per molecule, cyclic Jacobi, FP64) and D = 2 C_occ C_occ^T.
+ * diagonalisation of X^T F X (one thread block per molecule, cyclic Jacobi: FP64 for MESS_FP64,
+ * double-float - about 48 significant bits, on the FP32 units - for MESS_MIXED / MESS_FP32) and
+ * D = 2 C_occ C_occ^T.  The overlap matrix of X is always diagonalised in FP64.
  * With prec MESS_MIXED / MESS_FP32 the iterations use the reduced-precision builds and the reported
  * energy E_total is that of the final density from one full build in which the quartets above a ten
  * times lower split threshold (MESS_MIXED; every quartet for MESS_FP32) run in double-float

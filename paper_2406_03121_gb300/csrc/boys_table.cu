@@ -9,11 +9,11 @@
 
 #include "mess_internal.h"
 
-void mess_boys_table(std::vector<double>& tab)
+void mess_boys_table(std::vector<double>& tab, int nrow, double dt)
 {
-    tab.assign((size_t)MESS_BOYS_NROW * MESS_BOYS_NCOL, 0.0);
-    for (int k = 0; k < MESS_BOYS_NROW; ++k) {
-        const long double T = (long double)k * (long double)MESS_BOYS_DT;
+    tab.assign((size_t)nrow * MESS_BOYS_NCOL, 0.0);
+    for (int k = 0; k < nrow; ++k) {
+        const long double T = (long double)k * (long double)dt;
         const long double eT = expl(-T);
         const int top = MESS_BOYS_NF - 1;
         long double term = 1.0L / (2 * top + 1), sum = term;
@@ -41,7 +41,7 @@ extern "C" mess_status mess_boys_grid(double* out, int max_values, int* nrows, i
         return MESS_EINVAL;
     }
     std::vector<double> tab;
-    mess_boys_table(tab);
+    mess_boys_table(tab, MESS_BOYS_NROW, MESS_BOYS_DT);
     for (size_t i = 0; i < tab.size(); ++i) out[i] = tab[i];
     return MESS_OK;
 }

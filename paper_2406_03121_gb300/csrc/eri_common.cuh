@@ -1,6 +1,7 @@
 // Device-side building blocks shared by the generated per-class ERI code and the kernels:
 // primitive-pair tables, the Boys function F_m(T), and J/K accumulation helpers.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,7 +15,7 @@
 //       is the 2 pi^{5/2}/(zeta eta sqrt(zeta+eta)) prefactor of [00|00]^(m)),
 //   oo2z = 1/(2 zeta).
 // ------------------------------------------------------------------------------------------
-template <typename R> struct PrimPair { R zeta, Px, Py, Pz, PAx, PAy, PAz, K, oo2z; };
+template <typename R> struct PrimPair { R zeta, PAx, PAy, PAz, K, oo2z; };
 
 template <typename R> struct PairTable;
 
@@ -98,7 +99,7 @@ template <typename R> struct PairTable {
     const int* __restrict__ mn;              // [nmol] basis functions of the molecule (row stride)
     const double* __restrict__ boys64;       // Boys grid, FP64
     const float* __restrict__ boys32;        // Boys grid, FP32
-    const float4* __restrict__ boys32v;      // FP32 Taylor rows per order L: [L][row] {F_L..F_L+3}, {F_L+4, exp(-T_k), 0, 0}
+    const float4* __restrict__ boys32v;      // FP32 rows per order L: [L][row] {F_L, F_L+1, F_L+2, exp(-T_k)}
     const float2* __restrict__ boysdf;       // Boys grid, double-float (hi, lo)
     // per molecule: 0 = left the computation (a converged molecule of a batched SCF): its quartets
     // are skipped by the J/K kernels.  Null: every molecule takes part.
@@ -123,9 +124,8 @@ template <typename R> struct PairTable {
     {
         const PrimPairRec<R>& r = pp[i];
         PrimPair<R> o;
-        o.zeta = r.v[0]; o.Px = r.v[1]; o.Py = r.v[2]; o.Pz = r.v[3];
-        o.PAx = r.v[4]; o.PAy = r.v[5]; o.PAz = r.v[6]; o.K = r.v[7];
-        o.oo2z = r.v[8];
+        o.zeta = r.v[0]; o.PAx = r.v[1]; o.PAy = r.v[2]; o.PAz = r.v[3];
+        o.K = r.v[4]; o.oo2z = r.v[5];
         return o;
     }
 };
@@ -262,21 +262,35 @@ template <int L> __device__ __forceinline__ void boys_small_f32(float T, float* 
 {
     // nearest grid index without F2I / I2F conversions (those issue on the slow FP64 pipe): adding
     // 1.5 * 2^23 rounds T / dT to an integer held in the low mantissa bits (0 <= T / dT < 2^22)
-    const float r = fmaf(T, (float)MESS_BOYS_INV_DT, 12582912.0f);
+    const float r = fmaf(T, (float)MESS_BOYS32_INV_DT, 12582912.0f);
     const int k = __float_as_int(r) - 0x4B400000;
-    const float x = (r - 12582912.0f) * (float)MESS_BOYS_DT - T;
-    // the five Taylor coefficients F_L..F_L+4 at T_k and exp(-T_k) in two 16-byte loads
-    const float4* row = tabv + ((size_t)L * MESS_BOYS_NROW + k) * 2;
-    const float4 a = __ldg(row), b = __ldg(row + 1);
-    float s = b.x;
-    s = a.w + s * x * 0.25f;
+    const float kf = r - 12582912.0f;                  // k as a float, exactly
+    const float x = kf * (float)MESS_BOYS32_DT - T;    // T_k - T (T_k exact), |x| <= 1/32
+    // One 16-byte row: F_L, F_L+1, F_L+2 and exp(-T_k), each rounded once from the FP64 grid.
+    // F_L+3 and F_L+4 at T_k for the third- and fourth-order terms (at most 5e-6 and 4e-8 of F_L,
+    // so a few correct digits suffice; the fourth is kept because dropping it would bias every FP32
+    // integral with one sign) come from the upward recursion F_m+1 = ((2m+1) F_m - exp(-T_k)) / (2 T_k),
+    // F_m(0) = 1/(2m+1) at the first grid point.
+    const float4 a = __ldg(tabv + (size_t)L * MESS_BOYS32_NROW + k);
+    const float ek = a.w;
+    float f3, f4;
+    if (k > 0) {
+        const float h = __fdividef(0.5f * (float)MESS_BOYS32_INV_DT, kf);   // 1 / (2 T_k)
+        f3 = ((float)(2 * L + 5) * a.z - ek) * h;
+        f4 = ((float)(2 * L + 7) * f3 - ek) * h;
+    } else {
+        f3 = 1.0f / (float)(2 * L + 7);
+        f4 = 1.0f / (float)(2 * L + 9);
+    }
+    float s = f4;
+    s = f3 + s * x * 0.25f;
     s = a.z + s * x * (1.0f / 3);
     s = a.y + s * x * 0.5f;
     s = a.x + s * x;
     F[L] = s;
     if (L == 0) return;
-    const float ex = 1.0f + x * (1.0f + x * (0.5f + x * (1.0f / 6 + x * (1.0f / 24 + x * (1.0f / 120)))));
-    const float e = b.y * ex;
+    // exp(-T) = exp(-T_k) exp(x), exp(x) to fourth order (|x| <= 1/32: the next term is below 2e-9)
+    const float e = ek * (1.0f + x * (1.0f + x * (0.5f + x * (1.0f / 6 + x * (1.0f / 24)))));
     const float t2 = 2.0f * T;
 #pragma unroll
     for (int m = L; m >= 1; --m) F[m - 1] = (t2 * F[m] + e) * (1.0f / (2 * m - 1));

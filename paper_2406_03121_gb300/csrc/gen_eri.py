@@ -593,8 +593,9 @@ def emit_class_straight(cls):
     lines.append(f"    R acc[{nacc}];")
     lines.append(f"#pragma unroll")
     lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = R(0);")
-    lines.append("    const int b0 = P.pp_off[bp], b1 = b0 + (live ? P.pp_n[bp] : 0);   // !live: no primitive work")
     lines.append("    const int k0 = kv.k0, nk = kv.nk, k1 = k0 + nk;")
+    lines.append("    // !live, or a ket without primitives: no primitive work")
+    lines.append("    const int b0 = P.pp_off[bp], b1 = b0 + ((live && nk > 0) ? P.pp_n[bp] : 0);")
     lines.append("    // A - C in FP64, then P - Q = (P - A) - (Q - C) + (A - C): no absolute coordinates in R")
     lines.append("    const R ACx = kv.AC[0], ACy = kv.AC[1], ACz = kv.AC[2];")
     body = []
@@ -636,7 +637,7 @@ def emit_class_straight(cls):
     lines.append("    } else {")
     lines.append("    // the G lanes of a group split the primitive quartets (flattened index g, g + G, ...)")
     lines.append("    int ib = b0, ik = k0 + g;")
-    lines.append("    while (ik >= k1) { ik -= nk; ++ib; }")
+    lines.append("    while (ik >= k1 && ib < b1) { ik -= nk; ++ib; }")
     lines.append("#pragma unroll 1")
     lines.append("    while (ib < b1) {")
     lines.append("        {")
@@ -645,7 +646,7 @@ def emit_class_straight(cls):
     lines += body
     lines.append("        }")
     lines.append("        ik += G;")
-    lines.append("        while (ik >= k1) { ik -= nk; ++ib; }")
+    lines.append("        while (ik >= k1 && ib < b1) { ik -= nk; ++ib; }")
     lines.append("    }")
     lines.append("#pragma unroll")
     lines.append(f"    for (int k = 0; k < {nacc}; ++k) acc[k] = group_sum<G>(acc[k]);")
@@ -672,19 +673,62 @@ def emit_class_straight(cls):
     return "\n".join(lines) + "\n", info
 
 
+def df32_program(info):
+    """straight-line classes whose double-float quartets, one thread per quartet, run the op-program
+    interpreter: double-float takes about ten FP32 instructions per operation, and the straight-line
+    code of these classes would then overflow the instruction cache (the warps stall on fetch)"""
+    return info["mode"] == "straight" and info["vrr_flops"] + info["hrr_flops"] >= 250
+
+
 def emit_class(cls):
     body, info = emit_class_straight(cls)
-    if straight_line(info):
-        info["mode"] = "straight"
-        return body, info
     (la, lb), (lc, ld) = cls
     t = tag(cls)
+    if straight_line(info):
+        info["mode"] = "straight"
+        if not df32_program(info):
+            return body, info
+        # straight-line code for every arithmetic but double-float with one thread per quartet
+        pr = build_program(cls)
+        body = body.replace(f"__device__ __forceinline__ void eri_{t}(", f"__device__ __forceinline__ void eri_{t}_sl(", 1)
+        L = [body, f"// double-float, one thread per quartet: op program, {len(pr['vrr'])} VRR ops on {pr['nv']} "
+                   f"slots, {len(pr['hrr'])} HRR ops on {pr['nh']} slots"]
+        L += emit_program_tables(t, pr)
+        L.append("template <typename R, int BMODE, int G>")
+        L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, const KetView<R>& kv, int g, R* I, bool live = true)")
+        L.append("{")
+        L.append("    if constexpr (std::is_same<R, df32>::value && G == 1) {")
+        L.append("        (void)g;")
+        L.append(f"        eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
+                 f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kv, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, "
+                 f"fscaleh_{t}, fscalel_{t}, I, live);")
+        L.append("    } else {")
+        L.append(f"        eri_{t}_sl<R, BMODE, G>(P, bp, kv, g, I, live);")
+        L.append("    }")
+        L.append("}")
+        return "\n".join(L) + "\n", info
     pr = build_program(cls)
     info["mode"] = "program"
     info["nv_slots"], info["nh_slots"] = pr["nv"], pr["nh"]
     L = []
     L.append(f"// ---- class ({la}{lb}|{lc}{ld}): op program, {len(pr['vrr'])} VRR ops on {pr['nv']} slots, "
              f"{len(pr['hrr'])} HRR ops on {pr['nh']} slots")
+    L += emit_program_tables(t, pr)
+    L.append("template <typename R, int BMODE, int G>")
+    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, const KetView<R>& kv, int g, R* I, bool live = true)")
+    L.append("{")
+    L.append("    static_assert(G == 1, \"op-program classes run one thread per quartet\");")
+    L.append("    (void)g;")
+    L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
+             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kv, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, "
+             f"fscaleh_{t}, fscalel_{t}, I, live);")
+    L.append("}")
+    return "\n".join(L) + "\n", info
+
+
+def emit_program_tables(t, pr):
+    """device tables of one op program (VRR and HRR op words, output slots and scales)"""
+    L = []
     L.append(f"__device__ const uint4 vprog_{t}[{len(pr['vrr'])}] = {{")
     for (kind, tg, s1, s2, s3, s4, s5, d, m1, m2) in pr["vrr"]:
         w0 = kind | (d << 2) | (m1 << 4) | (m2 << 8) | (tg << 16)
@@ -702,16 +746,7 @@ def emit_class(cls):
     los = [float(np.float32(b - h)) for (_, b), h in zip(pr["fin"], his)]
     L.append(f"__device__ const float fscaleh_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(h) + "f" for h in his) + "};")
     L.append(f"__device__ const float fscalel_{t}[{len(pr['fin'])}] = {{" + ", ".join(repr(l) + "f" for l in los) + "};")
-    L.append("template <typename R, int BMODE, int G>")
-    L.append(f"__device__ __forceinline__ void eri_{t}(const PairTable<R>& P, int bp, const KetView<R>& kv, int g, R* I, bool live = true)")
-    L.append("{")
-    L.append("    static_assert(G == 1, \"op-program classes run one thread per quartet\");")
-    L.append("    (void)g;")
-    L.append(f"    eri_program<R, BMODE, {pr['L']}, {pr['nv']}, {pr['nh']}, {pr['nacc']}, {len(pr['vrr'])}, "
-             f"{len(pr['hrr'])}, {len(pr['fin'])}>(P, bp, kv, vprog_{t}, hprog_{t}, fslot_{t}, fscale_{t}, "
-             f"fscaleh_{t}, fscalel_{t}, I, live);")
-    L.append("}")
-    return "\n".join(L) + "\n", info
+    return L
 
 
 def emit_team(cls, info):
@@ -754,7 +789,27 @@ def team_capable(info):
     return info["nvrr"] >= 40
 
 
-def emit_digest(cls, unroll=True):
+def emit_digests(cls, info):
+    """The digestion of a class as the kernels call it (digest_<class>).  Straight-line classes stage
+    the density blocks in registers; the op-program classes, and the double-float path of the
+    straight-line classes that run the interpreter (df32_program), read D through the read-only
+    cache: a one-thread kernel that inlines the interpreter must not also stage density arrays."""
+    t = tag(cls)
+    if info["mode"] != "straight":
+        return emit_digest(cls, unroll=False)
+    if not df32_program(info):
+        return emit_digest(cls, unroll=True)
+    return (emit_digest(cls, unroll=True, name=f"digest_{t}_st") + "\n"
+            + emit_digest(cls, unroll=False, name=f"digest_{t}_ro") + "\n"
+            + "template <typename R>\n"
+            + f"__device__ __forceinline__ void digest_{t}(const R* I, const DigestCtx<R>& c, R s)\n"
+            + "{\n"
+            + f"    if constexpr (std::is_same<R, df32>::value) digest_{t}_ro<R>(I, c, s);\n"
+            + f"    else digest_{t}_st<R>(I, c, s);\n"
+            + "}\n")
+
+
+def emit_digest(cls, unroll=True, name=None):
     """J/K digestion of one shell quartet (see the kernel file for the accumulation convention).
     unroll=True: density blocks staged in registers, loops fully unrolled (small classes);
     unroll=False: compact loops reading the density through the read-only cache (large classes)."""
@@ -764,7 +819,7 @@ def emit_digest(cls, unroll=True):
     PR = "#pragma unroll" if unroll else "#pragma unroll 1"
     L = []
     L.append(f"template <typename R>")
-    L.append(f"__device__ __forceinline__ void digest_{t}(const R* I, const DigestCtx<R>& c, R s)")
+    L.append(f"__device__ __forceinline__ void {name or 'digest_' + t}(const R* I, const DigestCtx<R>& c, R s)")
     L.append("{")
     blocks = (("Dab", ("c.fa", na), ("c.fb", nb)), ("Dcd", ("c.fc", nc), ("c.fd", nd)),
               ("Dac", ("c.fa", na), ("c.fc", nc)), ("Dad", ("c.fa", na), ("c.fd", nd)),
@@ -813,7 +868,7 @@ def main(outdir):
         body, info = emit_class(cls)
         if team_capable(info) or info["mode"] == "program":
             body += "\n" + emit_team(cls, info)
-        dig = emit_digest(cls, unroll=(info['mode'] == 'straight'))
+        dig = emit_digests(cls, info)
         path = os.path.join(outdir, f"eri_class_{info['tag']}.cuh")
         text = ("// Generated by gen_eri.py: do not edit.\n#pragma once\n#include \"eri_common.cuh\"\n\n"
                 + body + "\n" + dig)

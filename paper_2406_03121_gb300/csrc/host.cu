@@ -6,12 +6,15 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <fstream>
 #include <map>
 #include <mutex>
 #include <numeric>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_profiler_api.h>
@@ -33,6 +36,28 @@ void mess_set_error(const char* fmt, ...)
 }
 
 extern "C" const char* mess_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------------------------------ phase timing
+static double wall_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+PhaseTimer::PhaseTimer(cudaStream_t stream) : s(stream)
+{
+    const char* e = getenv("MESS_TIMING");
+    on = e && e[0] == '1';
+    t = on ? wall_ms() : 0.0;
+}
+
+void PhaseTimer::mark(const char* label)
+{
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    const double now = wall_ms();
+    fprintf(stderr, "[mess] %s: %.2f ms\n", label, now - t);
+    t = now;
+}
 
 // ------------------------------------------------------------------------------------------ basis file
 namespace {
@@ -151,100 +176,140 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
     BinSet& B = b->bins;
     if (B.tau == tau && B.tau64 == tau64 && B.split == split && B.active_version == b->active_version) return MESS_OK;
     B.parts.clear();
-    std::vector<int> bra, kbeg;
-    std::vector<long long> offs;
-    for (int p1 = 0; p1 < MESS_NUM_PCLASS; ++p1) {
-        for (int p2 = 0; p2 <= p1; ++p2) {
-        for (int g1 = 0; g1 < MESS_NGROUP; ++g1) {
-        for (int g2 = 0; g2 < MESS_NGROUP; ++g2) {
-            // unordered pairs of pairs of one class: list g1 x list g2 for g1 > g2, triangle for g1 == g2
-            if (p1 == p2 && g2 > g1) continue;
-            const int L1 = p1 * MESS_NGROUP + g1, L2 = p2 * MESS_NGROUP + g2;
-            const std::vector<int>& bl = b->class_list[L1];
-            const std::vector<int>& kl = b->class_list[L2];
-            if (bl.empty() || kl.empty()) continue;
-            const bool same = p1 == p2 && g1 == g2;
-            const int nk = (int)kl.size();
-            std::vector<double> qk(nk);
-            std::vector<long long> fpre(nk + 1, 0), ppre(nk + 1, 0);
-            for (int j = 0; j < nk; ++j) {
-                const int pk = kl[j];
-                qk[j] = b->Q[pk];
-                const int nc = ncart(b->shells[b->pair_a[pk]].l), nd = ncart(b->shells[b->pair_b[pk]].l);
-                const long long nfp = b->pair_a[pk] == b->pair_b[pk] ? (long long)nc * (nc + 1) / 2 : (long long)nc * nd;
-                fpre[j + 1] = fpre[j] + nfp;
-                ppre[j + 1] = ppre[j] + b->pp_n[pk];
-            }
-            const int nparts = split == 2 ? 2 : 1;
-            for (int part = 0; part < nparts; ++part) {
-                const int fp64 = split == 0 ? 1 : (split == 1 ? 0 : (part == 0 ? 1 : 0));
-                BinPart bp;
-                bp.qclass = qclass_of(p1, p2);
-                bp.fp64 = fp64;
-                bp.bra_off = (int)bra.size();
-                bp.ket_list = L2;
-                bp.offs_off = offs.size();
-                bp.total = 0;
-                bp.fn_quartets = 0;
-                bp.prim_quartets = 0;
-                for (int m = 0; m < b->nmol; ++m) {
-                    if (!b->active[m]) continue;
-                    const int bs0 = b->class_seg[L1][m], bs1 = b->class_seg[L1][m + 1];
-                    const int ks0 = b->class_seg[L2][m], ks1 = b->class_seg[L2][m + 1];
-                    if (bs1 == bs0 || ks1 == ks0) continue;
-                    // kets j in [ks0, ks1) (Q descending) with qi * qk[j] >= t: a prefix of the segment
-                    auto count_ge = [&](double qi, double t) -> int {
-                        if (t <= 0.0) return ks1 - ks0;
-                        int lo = ks0, hi = ks1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) / 2;
-                            if (qi * qk[mid] >= t) lo = mid + 1; else hi = mid;
-                        }
-                        return lo - ks0;
-                    };
-                    for (int i = bs0; i < bs1; ++i) {
-                        const int il = i - bs0;
-                        const int pb = bl[i];
-                        const double qi = b->Q[pb];
-                        int cnt = count_ge(qi, tau);
-                        if (same) cnt = std::min(cnt, il + 1);
-                        int beg = 0, end = cnt;
-                        if (split == 2) {
-                            const int c64 = tau64 > 0.0 ? std::min(count_ge(qi, tau64), cnt) : 0;
-                            if (part == 0) end = c64; else beg = c64;
-                        }
-                        if (end <= beg) continue;
-                        bra.push_back(pb);
-                        kbeg.push_back(ks0 + beg);
-                        offs.push_back(bp.total);
-                        bp.total += end - beg;
-                        const int na = ncart(b->shells[b->pair_a[pb]].l), nb = ncart(b->shells[b->pair_b[pb]].l);
-                        const long long nfb = b->pair_a[pb] == b->pair_b[pb] ? (long long)na * (na + 1) / 2 : (long long)na * nb;
-                        bp.fn_quartets += nfb * (fpre[ks0 + end] - fpre[ks0 + beg]);
-                        if (same && beg <= il && il < end) bp.fn_quartets += nfb * (nfb + 1) / 2 - nfb * nfb;
-                        bp.prim_quartets += (long long)b->pp_n[pb] * (ppre[ks0 + end] - ppre[ks0 + beg]);
-                    }
-                }
-                bp.nbra = (int)bra.size() - bp.bra_off;
-                offs.push_back(bp.total);
-                // heavily contracted quartets: split the primitive loop over 8 lanes
-                const bool straight = MESS_QCLASS[bp.qclass].straight != 0;
-                const double avg = bp.total > 0 ? (double)bp.prim_quartets / (double)bp.total : 0.0;
-                // lanes per quartet: 8 for long primitive loops; 4 for medium loops of parts too small to
-                // fill the GPU one thread per quartet (measured: slower on parts of millions of quartets)
-                bp.G = !straight ? 1 : (avg >= 24.0 ? 8 : ((avg >= 6.0 && bp.total < (1LL << 18)) ? 4 : 1));
-                // warp per quartet: always for the op-program classes; for small FP64 parts of the classes
-                // with at least 40 VRR entries (too few quartets to fill the GPU one thread each:
-                // measured better below about 2e6 quartets x VRR entries, worse above)
-                const double work = (double)bp.total * MESS_QCLASS[bp.qclass].nvrr;
-                bp.team = (!straight || (fp64 && MESS_QCLASS[bp.qclass].team && bp.G == 1 && work < 2e6)) ? 1 : 0;
-                if (bp.nbra > 0) B.parts.push_back(bp);
-                else offs.resize(bp.offs_off);
-            }
-        }
-        }
+    // per ket list (pair class x primitive group): Q, and prefix sums of unique function pairs and of
+    // primitive pairs, in list order
+    const int NL = MESS_NUM_PCLASS * MESS_NGROUP;
+    std::vector<std::vector<long long>> fpre_l(NL), ppre_l(NL);
+    for (int Lk = 0; Lk < NL; ++Lk) {
+        const std::vector<int>& kl = b->class_list[Lk];
+        const int nk = (int)kl.size();
+        fpre_l[Lk].assign(nk + 1, 0);
+        ppre_l[Lk].assign(nk + 1, 0);
+        for (int j = 0; j < nk; ++j) {
+            const int pk = kl[j];
+            const int nc = ncart(b->shells[b->pair_a[pk]].l), nd = ncart(b->shells[b->pair_b[pk]].l);
+            const long long nfp = b->pair_a[pk] == b->pair_b[pk] ? (long long)nc * (nc + 1) / 2 : (long long)nc * nd;
+            fpre_l[Lk][j + 1] = fpre_l[Lk][j] + nfp;
+            ppre_l[Lk][j + 1] = ppre_l[Lk][j] + b->pp_n[pk];
         }
     }
+    // One task per unordered pair of lists (list g1 x list g2 for g1 > g2, the triangle for g1 == g2
+    // within one pair class); each builds its parts (FP64-class / reduced-precision split) into its
+    // own arrays.  Tasks are independent and run on host threads; the parts are concatenated in task
+    // order, so the bins do not depend on the threading.
+    struct Task { int p1, p2, g1, g2; std::vector<BinPart> parts; std::vector<int> bra, kbeg; std::vector<long long> offs; };
+    std::vector<Task> tasks;
+    for (int p1 = 0; p1 < MESS_NUM_PCLASS; ++p1)
+        for (int p2 = 0; p2 <= p1; ++p2)
+            for (int g1 = 0; g1 < MESS_NGROUP; ++g1)
+                for (int g2 = 0; g2 < MESS_NGROUP; ++g2) {
+                    if (p1 == p2 && g2 > g1) continue;
+                    if (b->class_list[p1 * MESS_NGROUP + g1].empty() || b->class_list[p2 * MESS_NGROUP + g2].empty()) continue;
+                    tasks.push_back(Task{p1, p2, g1, g2, {}, {}, {}, {}});
+                }
+    auto run_task = [&](Task& T) {
+        const int p1 = T.p1, p2 = T.p2, g1 = T.g1, g2 = T.g2;
+        const int L1 = p1 * MESS_NGROUP + g1, L2 = p2 * MESS_NGROUP + g2;
+        const std::vector<int>& bl = b->class_list[L1];
+        const std::vector<long long>& fpre = fpre_l[L2];
+        const std::vector<long long>& ppre = ppre_l[L2];
+        const std::vector<int>& kl = b->class_list[L2];
+        const bool same = p1 == p2 && g1 == g2;
+        std::vector<int>& bra = T.bra;
+        std::vector<int>& kbeg = T.kbeg;
+        std::vector<long long>& offs = T.offs;
+        const int nparts = split == 2 ? 2 : 1;
+        for (int part = 0; part < nparts; ++part) {
+            const int fp64 = split == 0 ? 1 : (split == 1 ? 0 : (part == 0 ? 1 : 0));
+            BinPart bp;
+            bp.qclass = qclass_of(p1, p2);
+            bp.fp64 = fp64;
+            bp.bra_off = (int)bra.size();
+            bp.ket_list = L2;
+            bp.offs_off = offs.size();
+            bp.total = 0;
+            bp.fn_quartets = 0;
+            bp.prim_quartets = 0;
+            for (int m = 0; m < b->nmol; ++m) {
+                if (!b->active[m]) continue;
+                const int bs0 = b->class_seg[L1][m], bs1 = b->class_seg[L1][m + 1];
+                const int ks0 = b->class_seg[L2][m], ks1 = b->class_seg[L2][m + 1];
+                if (bs1 == bs0 || ks1 == ks0) continue;
+                // kets j in [ks0, ks1) (Q descending) with qi * Q_j >= t: a prefix of the segment
+                auto count_ge = [&](double qi, double t) -> int {
+                    if (t <= 0.0) return ks1 - ks0;
+                    int lo = ks0, hi = ks1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) / 2;
+                        if (qi * b->Q[kl[mid]] >= t) lo = mid + 1; else hi = mid;
+                    }
+                    return lo - ks0;
+                };
+                for (int i = bs0; i < bs1; ++i) {
+                    const int il = i - bs0;
+                    const int pb = bl[i];
+                    const double qi = b->Q[pb];
+                    int cnt = count_ge(qi, tau);
+                    if (same) cnt = std::min(cnt, il + 1);
+                    int beg = 0, end = cnt;
+                    if (split == 2) {
+                        const int c64 = tau64 > 0.0 ? std::min(count_ge(qi, tau64), cnt) : 0;
+                        if (part == 0) end = c64; else beg = c64;
+                    }
+                    if (end <= beg) continue;
+                    bra.push_back(pb);
+                    kbeg.push_back(ks0 + beg);
+                    offs.push_back(bp.total);
+                    bp.total += end - beg;
+                    const int na = ncart(b->shells[b->pair_a[pb]].l), nb = ncart(b->shells[b->pair_b[pb]].l);
+                    const long long nfb = b->pair_a[pb] == b->pair_b[pb] ? (long long)na * (na + 1) / 2 : (long long)na * nb;
+                    bp.fn_quartets += nfb * (fpre[ks0 + end] - fpre[ks0 + beg]);
+                    if (same && beg <= il && il < end) bp.fn_quartets += nfb * (nfb + 1) / 2 - nfb * nfb;
+                    bp.prim_quartets += (long long)b->pp_n[pb] * (ppre[ks0 + end] - ppre[ks0 + beg]);
+                }
+            }
+            bp.nbra = (int)bra.size() - bp.bra_off;
+            offs.push_back(bp.total);
+            // heavily contracted quartets: split the primitive loop over 8 lanes
+            const bool straight = MESS_QCLASS[bp.qclass].straight != 0;
+            const double avg = bp.total > 0 ? (double)bp.prim_quartets / (double)bp.total : 0.0;
+            // lanes per quartet: 8 for long primitive loops; 4 for medium loops of parts too small to
+            // fill the GPU one thread per quartet (measured: slower on parts of millions of quartets)
+            bp.G = !straight ? 1 : (avg >= 24.0 ? 8 : ((avg >= 6.0 && bp.total < (1LL << 18)) ? 4 : 1));
+            // warp per quartet: always for the op-program classes; for small FP64 parts of the classes
+            // with at least 40 VRR entries (too few quartets to fill the GPU one thread each:
+            // measured better below about 2e6 quartets x VRR entries, worse above)
+            const double work = (double)bp.total * MESS_QCLASS[bp.qclass].nvrr;
+            bp.team = (!straight || (fp64 && MESS_QCLASS[bp.qclass].team && bp.G == 1 && work < 2e6)) ? 1 : 0;
+            if (bp.nbra > 0) T.parts.push_back(bp);
+            else offs.resize(bp.offs_off);
+        }
+    };
+    {
+        std::atomic<size_t> next(0);
+        auto worker = [&]() {
+            for (size_t t; (t = next.fetch_add(1)) < tasks.size();) run_task(tasks[t]);
+        };
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        const int nthr = std::max(1, std::min({hw, 32, (int)tasks.size()}));
+        std::vector<std::thread> workers;
+        for (int t = 1; t < nthr; ++t) workers.emplace_back(worker);
+        worker();
+        for (auto& w : workers) w.join();
+    }
+    std::vector<int> bra, kbeg;
+    std::vector<long long> offs;
+    for (Task& T : tasks) {
+        for (BinPart bp : T.parts) {
+            bp.bra_off += (int)bra.size();
+            bp.offs_off += offs.size();
+            B.parts.push_back(bp);
+        }
+        bra.insert(bra.end(), T.bra.begin(), T.bra.end());
+        kbeg.insert(kbeg.end(), T.kbeg.begin(), T.kbeg.end());
+        offs.insert(offs.end(), T.offs.begin(), T.offs.end());
+    }
+    tasks.clear();
     // per part, the bra of every 32nd quartet
     std::vector<int> seg;
     for (BinPart& p : B.parts) {
@@ -417,70 +482,166 @@ static mess_status build_pairs(mess_basis* b)
                 b->f_local.push_back(s.fl + k);
             }
     }
-    std::vector<PrimPairRec<double>> pp64;
-    std::vector<PrimPairRec<float>> pp32;
-    std::vector<PrimPairRec<df32>> ppdf;
+    const double kpref = sqrt(2.0) * pow(M_PI, 1.25);
+    // Primitive-pair screening.  The product of two primitives a, b (coefficients c_a, c_b) is a
+    // Gaussian distribution of total weight S_ab = |c_a c_b| exp(-alpha beta/zeta |AB|^2) (pi/zeta)^(3/2);
+    // the Coulomb integral of two such s-type distributions is S_ab S_cd 2 sqrt(rho/pi) F_0 <=
+    // M_ab M_cd with M = sqrt(2) (zeta/pi)^(1/4) S.  A primitive pair whose M times the largest M of
+    // the basis is below MESS_PRIM_EPS contributes nothing measurable to any integral (the margin
+    // of MESS_PRIM_EPS covers the polynomial factors of p and d functions and the number of
+    // primitive quartets of a shell quartet), and is left out of the pair's primitive list.
+    auto prim_weight = [](const HostShell& sa, const HostShell& sb, int i, int j, double ab2) {
+        const double al = sa.alpha[i], be = sb.alpha[j], z = al + be;
+        const double u = M_PI / z;   // M = sqrt(2) (zeta/pi)^(1/4) (pi/zeta)^(3/2) |c_a c_b| exp(..) = sqrt(2) u^(5/4) ...
+        return sqrt(2.0) * u * sqrt(sqrt(u)) * fabs(sa.coef[i] * sb.coef[j]) * exp(-al * be / z * ab2);
+    };
+    double Mmax = 0.0;
+    for (int m = 0; m < b->nmol; ++m) {
+        const int s0 = b->mol_shell_off[m], s1 = s0 + b->mol_shell_n[m];
+        for (int A = s0; A < s1; ++A)       // the scale: the largest weight of a primitive with itself
+            for (int i = 0; i < b->shells[A].K; ++i)
+                for (int j = 0; j < b->shells[A].K; ++j)
+                    Mmax = std::max(Mmax, prim_weight(b->shells[A], b->shells[A], i, j, 0.0));
+    }
+    // The pairs of molecules [m0, m1): shell pairs A >= B (canonical order) of each molecule, with
+    // their kept primitive pairs.  Molecules are independent, so contiguous molecule ranges are built
+    // on host threads and concatenated in molecule order (the result does not depend on the split).
+    struct Chunk {
+        std::vector<int> pa, pb, pcls, pmol, pn, fa, fb, same;
+        std::vector<double> AB, Ccen;
+        std::vector<float> ABf, Cf;
+        std::vector<PrimPairRec<double>> pp64;
+        std::vector<PrimPairRec<float>> pp32;
+        std::vector<PrimPairRec<df32>> ppdf;
+    };
+    auto build_chunk = [&](int m0, int m1, Chunk& c) {
+        std::vector<double> wts;
+        for (int m = m0; m < m1; ++m) {
+            const int s0 = b->mol_shell_off[m], s1 = s0 + b->mol_shell_n[m];
+            for (int A = s0; A < s1; ++A) {
+                for (int B = s0; B < s1; ++B) {
+                    const HostShell& sa = b->shells[A];
+                    const HostShell& sb = b->shells[B];
+                    const bool canonical = sa.l > sb.l || (sa.l == sb.l && A >= B);
+                    if (!canonical) continue;
+                    c.pa.push_back(A);
+                    c.pb.push_back(B);
+                    c.pcls.push_back(pclass_of(sa.l, sb.l));
+                    c.pmol.push_back(m);
+                    double ab2 = 0.0;
+                    for (int x = 0; x < 3; ++x) {
+                        const double abx = sa.R[x] - sb.R[x];
+                        ab2 += abx * abx;
+                        c.AB.push_back(abx);
+                        c.ABf.push_back((float)abx);
+                        c.Ccen.push_back(sa.R[x]);
+                    }
+                    for (int x = 0; x < 3; ++x) c.Cf.push_back((float)sa.R[x]);
+                    for (int x = 0; x < 3; ++x) c.Cf.push_back((float)(sa.R[x] - (double)(float)sa.R[x]));
+                    // kept primitive pairs; at least the heaviest one, so that no pair is empty
+                    int npp = 0, heavy = 0;
+                    double wmax = -1.0;
+                    wts.resize((size_t)sa.K * sb.K);
+                    for (int i = 0; i < sa.K; ++i)
+                        for (int j = 0; j < sb.K; ++j) {
+                            const double w = prim_weight(sa, sb, i, j, ab2);
+                            wts[(size_t)i * sb.K + j] = w;
+                            if (w > wmax) { wmax = w; heavy = i * sb.K + j; }
+                        }
+                    for (int i = 0; i < sa.K; ++i)
+                        for (int j = 0; j < sb.K; ++j) {
+                            if (wts[(size_t)i * sb.K + j] * Mmax < MESS_PRIM_EPS && i * sb.K + j != heavy) continue;
+                            ++npp;
+                            const double al = sa.alpha[i], be = sb.alpha[j], z = al + be;
+                            PrimPairRec<double> r{};
+                            r.v[0] = z;
+                            for (int x = 0; x < 3; ++x) {
+                                const double P = (al * sa.R[x] + be * sb.R[x]) / z;
+                                r.v[1 + x] = P - sa.R[x];
+                            }
+                            r.v[4] = kpref * sa.coef[i] * sb.coef[j] * exp(-al * be / z * ab2) / z;
+                            r.v[5] = 0.5 / z;
+                            c.pp64.push_back(r);
+                            PrimPairRec<float> f{};
+                            PrimPairRec<df32> g;
+                            for (int k = 0; k < 8; ++k) {
+                                f.v[k] = (float)r.v[k];
+                                g.v[k].hi = (float)r.v[k];
+                                g.v[k].lo = (float)(r.v[k] - (double)g.v[k].hi);
+                            }
+                            c.pp32.push_back(f);
+                            c.ppdf.push_back(g);
+                        }
+                    c.pn.push_back(npp);
+                    c.fa.push_back(sa.fl);
+                    c.fb.push_back(sb.fl);
+                    c.same.push_back(A == B ? 1 : 0);
+                }
+            }
+        }
+    };
+    // molecule ranges of about equal work (shells squared) for the host threads
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nthr = std::max(1, std::min({hw, 32, b->nmol}));
+    std::vector<int> cut(1, 0);
+    {
+        double tot = 0.0, acc = 0.0;
+        for (int m = 0; m < b->nmol; ++m) tot += (double)b->mol_shell_n[m] * b->mol_shell_n[m];
+        for (int m = 0; m < b->nmol && (int)cut.size() < nthr; ++m) {
+            acc += (double)b->mol_shell_n[m] * b->mol_shell_n[m];
+            if (acc >= tot * (double)cut.size() / nthr && m + 1 < b->nmol) cut.push_back(m + 1);
+        }
+        cut.push_back(b->nmol);
+    }
+    std::vector<Chunk> chunks(cut.size() - 1);
+    {
+        std::vector<std::thread> workers;
+        for (size_t t = 1; t < chunks.size(); ++t)
+            workers.emplace_back(build_chunk, cut[t], cut[t + 1], std::ref(chunks[t]));
+        build_chunk(cut[0], cut[1], chunks[0]);
+        for (auto& w : workers) w.join();
+    }
+    // concatenation in molecule order; the primitive records go to the device chunk by chunk
     std::vector<double> AB, Ccen;
     std::vector<float> ABf, Cf;
     std::vector<int> fa, fb, same;
-    const double kpref = sqrt(2.0) * pow(M_PI, 1.25);
-    for (int m = 0; m < b->nmol; ++m) {
-        const int s0 = b->mol_shell_off[m], s1 = s0 + b->mol_shell_n[m];
-        for (int A = s0; A < s1; ++A) {
-            for (int B = s0; B < s1; ++B) {
-                const HostShell& sa = b->shells[A];
-                const HostShell& sb = b->shells[B];
-                const bool canonical = sa.l > sb.l || (sa.l == sb.l && A >= B);
-                if (!canonical) continue;
-                b->npair++;
-                b->pair_a.push_back(A);
-                b->pair_b.push_back(B);
-                b->pair_class.push_back(pclass_of(sa.l, sb.l));
-                b->pair_mol.push_back(m);
-                b->pp_off.push_back((int)pp64.size());
-                double ab[3], ab2 = 0.0;
-                for (int x = 0; x < 3; ++x) {
-                    ab[x] = sa.R[x] - sb.R[x];
-                    ab2 += ab[x] * ab[x];
-                    AB.push_back(ab[x]);
-                    ABf.push_back((float)ab[x]);
-                    Ccen.push_back(sa.R[x]);
-                }
-                for (int x = 0; x < 3; ++x) Cf.push_back((float)sa.R[x]);
-                for (int x = 0; x < 3; ++x) Cf.push_back((float)(sa.R[x] - (double)(float)sa.R[x]));
-                for (int i = 0; i < sa.K; ++i)
-                    for (int j = 0; j < sb.K; ++j) {
-                        const double al = sa.alpha[i], be = sb.alpha[j], z = al + be;
-                        PrimPairRec<double> r{};
-                        r.v[0] = z;
-                        for (int x = 0; x < 3; ++x) {
-                            const double P = (al * sa.R[x] + be * sb.R[x]) / z;
-                            r.v[1 + x] = P;
-                            r.v[4 + x] = P - sa.R[x];
-                        }
-                        r.v[7] = kpref * sa.coef[i] * sb.coef[j] * exp(-al * be / z * ab2) / z;
-                        r.v[8] = 0.5 / z;
-                        pp64.push_back(r);
-                        PrimPairRec<float> f{};
-                        PrimPairRec<df32> g;
-                        for (int k = 0; k < 12; ++k) {
-                            f.v[k] = (float)r.v[k];
-                            g.v[k].hi = (float)r.v[k];
-                            g.v[k].lo = (float)(r.v[k] - (double)g.v[k].hi);
-                        }
-                        pp32.push_back(f);
-                        ppdf.push_back(g);
-                    }
-                b->pp_n.push_back(sa.K * sb.K);
-                fa.push_back(sa.fl);
-                fb.push_back(sb.fl);
-                same.push_back(A == B ? 1 : 0);
+    size_t npp_tot = 0;
+    for (const Chunk& c : chunks) {
+        for (size_t k = 0; k < c.pa.size(); ++k) {
+            b->pp_off.push_back((int)npp_tot);
+            npp_tot += (size_t)c.pn[k];
+        }
+        b->pair_a.insert(b->pair_a.end(), c.pa.begin(), c.pa.end());
+        b->pair_b.insert(b->pair_b.end(), c.pb.begin(), c.pb.end());
+        b->pair_class.insert(b->pair_class.end(), c.pcls.begin(), c.pcls.end());
+        b->pair_mol.insert(b->pair_mol.end(), c.pmol.begin(), c.pmol.end());
+        b->pp_n.insert(b->pp_n.end(), c.pn.begin(), c.pn.end());
+        AB.insert(AB.end(), c.AB.begin(), c.AB.end());
+        Ccen.insert(Ccen.end(), c.Ccen.begin(), c.Ccen.end());
+        ABf.insert(ABf.end(), c.ABf.begin(), c.ABf.end());
+        Cf.insert(Cf.end(), c.Cf.begin(), c.Cf.end());
+        fa.insert(fa.end(), c.fa.begin(), c.fa.end());
+        fb.insert(fb.end(), c.fb.begin(), c.fb.end());
+        same.insert(same.end(), c.same.begin(), c.same.end());
+    }
+    if (npp_tot > (size_t)INT32_MAX) { mess_set_error("too many primitive pairs (%zu)", npp_tot); return MESS_EINVAL; }
+    b->npair = (int)b->pair_a.size();
+    MESS_CUDA_TRY(b->d_pp64.alloc(npp_tot));
+    MESS_CUDA_TRY(b->d_pp32.alloc(npp_tot));
+    MESS_CUDA_TRY(b->d_ppdf.alloc(npp_tot));
+    {
+        size_t off = 0;
+        for (const Chunk& c : chunks) {
+            const size_t k = c.pp64.size();
+            if (k) {
+                MESS_CUDA_TRY(cudaMemcpy(b->d_pp64.p + off, c.pp64.data(), k * sizeof(c.pp64[0]), cudaMemcpyHostToDevice));
+                MESS_CUDA_TRY(cudaMemcpy(b->d_pp32.p + off, c.pp32.data(), k * sizeof(c.pp32[0]), cudaMemcpyHostToDevice));
+                MESS_CUDA_TRY(cudaMemcpy(b->d_ppdf.p + off, c.ppdf.data(), k * sizeof(c.ppdf[0]), cudaMemcpyHostToDevice));
             }
+            off += k;
         }
     }
-    MESS_CUDA_TRY(b->d_pp64.upload(pp64));
-    MESS_CUDA_TRY(b->d_pp32.upload(pp32));
-    MESS_CUDA_TRY(b->d_ppdf.upload(ppdf));
+    chunks.clear();
     MESS_CUDA_TRY(b->d_pp_off.upload(b->pp_off));
     MESS_CUDA_TRY(b->d_pp_n.upload(b->pp_n));
     MESS_CUDA_TRY(b->d_AB.upload(AB));
@@ -509,18 +670,19 @@ static mess_status build_pairs(mess_basis* b)
     }
     MESS_CUDA_TRY(b->d_pair_rec.upload(b->pair_rec));
     std::vector<double> tab;
-    mess_boys_table(tab);
+    mess_boys_table(tab, MESS_BOYS_NROW, MESS_BOYS_DT);
     MESS_CUDA_TRY(b->d_boys64.upload(tab));
     std::vector<float> tab32(tab.begin(), tab.end());
     MESS_CUDA_TRY(b->d_boys32.upload(tab32));
-    // FP32 Taylor rows per order L (two float4 per grid row): F_L..F_L+3 | F_L+4, exp(-T_k), 0, 0
-    std::vector<float4> tabv((size_t)MESS_BOYS_NL * MESS_BOYS_NROW * 2);
+    // FP32 rows per order L on the finer grid, one float4 per row: F_L, F_L+1, F_L+2, exp(-T_k)
+    std::vector<double> fine;
+    mess_boys_table(fine, MESS_BOYS32_NROW, MESS_BOYS32_DT);
+    std::vector<float4> tabv((size_t)MESS_BOYS_NL * MESS_BOYS32_NROW);
     for (int L = 0; L < MESS_BOYS_NL; ++L)
-        for (int k = 0; k < MESS_BOYS_NROW; ++k) {
-            const double* row = tab.data() + (size_t)k * MESS_BOYS_NCOL;
-            float4* o = tabv.data() + ((size_t)L * MESS_BOYS_NROW + k) * 2;
-            o[0] = make_float4((float)row[L], (float)row[L + 1], (float)row[L + 2], (float)row[L + 3]);
-            o[1] = make_float4((float)row[L + 4], (float)row[MESS_BOYS_NF], 0.f, 0.f);
+        for (int k = 0; k < MESS_BOYS32_NROW; ++k) {
+            const double* row = fine.data() + (size_t)k * MESS_BOYS_NCOL;
+            tabv[(size_t)L * MESS_BOYS32_NROW + k] =
+                make_float4((float)row[L], (float)row[L + 1], (float)row[L + 2], (float)row[MESS_BOYS_NF]);
         }
     MESS_CUDA_TRY(b->d_boys32v.upload(tabv));
     std::vector<float2> tabdf(tab.size());
@@ -773,8 +935,11 @@ mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basi
         if (!s || s->nmol != 1) { delete b; mess_set_error("batch entry %d is not a single-molecule basis", m); return MESS_EINVAL; }
         add_molecule(b, s->Z, s->xyz, s->shells);
     }
+    PhaseTimer tm(nullptr);
     mess_status st = build_pairs(b);
+    tm.mark("batched basis: primitive pairs");
     if (st == MESS_OK) st = build_schwarz(b);
+    tm.mark("batched basis: Schwarz factors");
     if (st != MESS_OK) { mess_free_basis(b); delete b; return st; }
     b->gpu_ready = true;
     *out = b;

@@ -12,14 +12,24 @@
 #define MESS_BOYS_NCOL (MESS_BOYS_NF + 1)
 #define MESS_BOYS_NROW 362
 #define MESS_BOYS_NL 9            // orders L = 0..8 of the FP32 Taylor rows (L = la+lb+lc+ld <= 8)
+// FP32 rows: T_k = k * MESS_BOYS32_DT with a step that FP32 holds exactly (1/16: T_k - T is then
+// formed with one rounding; a step of 0.1 or 0.05 rounded to FP32 shifts x by up to 5e-7 at the far
+// end of the grid, a one-signed error of up to 1e-7 in F_L); F_L, F_L+1, F_L+2 and exp(-T_k) in one
+// 16-byte row (Taylor order 4, F_L+3 and F_L+4 from the upward recursion); rows up to T = MESS_BOYS_TMAX32.
+#define MESS_BOYS32_DT 0.0625
+#define MESS_BOYS32_INV_DT 16.0
+#define MESS_BOYS32_NROW 482
+
+#define MESS_PRIM_EPS 1e-18       // primitive pairs below this weight bound are left out (build_pairs)
 
 #define MESS_LMAX 2               // s, p, Cartesian d
 #define MESS_NUM_PCLASS 6         // pair classes (la,lb): ss ps pp ds dp dd
 #define MESS_NGROUP 3             // primitive-pair count groups: <= 3, 4..12, >= 13
 #define MESS_TEAM_WARPS 4         // warps (one shell quartet each) per block of the large-class kernels
 
-// One primitive pair: zeta, Px, Py, Pz, PAx, PAy, PAz, K, 1/(2 zeta) (+ padding to 16 bytes).
-template <typename R> struct alignas(16) PrimPairRec { R v[12]; };
+// One primitive pair: zeta, PAx, PAy, PAz (P - A, P the Gaussian product centre), K, 1/(2 zeta), and
+// two padding slots: 32 bytes in FP32 (one sector per record), 64 in FP64 and double-float.
+template <typename R> struct alignas(32) PrimPairRec { R v[8]; };
 
 // Everything a J/K kernel reads about the ket pair of a quartet, in one 112-byte record (seven 16-byte
 // loads at most; the arithmetic reads only the ones it needs).  Stored per pair (pair order) and per

@@ -12,6 +12,18 @@
 
 void mess_set_error(const char* fmt, ...);
 
+// Phase timing of the host-driven calls, for users who want to see where a call spends its time:
+// with MESS_TIMING=1 in the environment, every mark() synchronises the given stream and prints the
+// host wall time since the previous mark to stderr ("[mess] <label>: <ms> ms").  Off by default:
+// then mark() does nothing (no synchronisation).
+struct PhaseTimer {
+    bool on;
+    cudaStream_t s;
+    double t;
+    explicit PhaseTimer(cudaStream_t stream);
+    void mark(const char* label);
+};
+
 #define MESS_CUDA_TRY(expr)                                                                      \
     do {                                                                                          \
         cudaError_t e_ = (expr);                                                                  \
@@ -182,7 +194,8 @@ cudaError_t mess_launch_symmetrise_jk(const mess_basis* b, double* J, double* K,
 // FP32 and double-float copies of the packed density (either output may be null)
 cudaError_t mess_launch_convert_density(const double* D, float* D32, float2* Ddf, long long count, cudaStream_t s);
 // Boys tables (boys_table.cu): rows x MESS_BOYS_NCOL
-void mess_boys_table(std::vector<double>& tab);
+// F_0..F_{NF-1} and exp(-T) at T_k = k * dt, k < nrow (row-major, MESS_BOYS_NCOL columns)
+void mess_boys_table(std::vector<double>& tab, int nrow, double dt);
 // bins (host.cu)
 mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split);
 // derivative basis (host.cu) of a single-molecule basis whose shells have l < MESS_LMAX: the shells of b

@@ -325,45 +325,81 @@ __global__ void k_converge(const double* __restrict__ E, const double* __restric
     Eold[m] = e;
 }
 
+// Element arithmetic of the Jacobi eigensolver: FP64, or double-float (hi + lo FP32 pairs, about
+// 48 significant bits) for the reduced-precision SCF, where the eigensolver then runs on the FP32
+// units instead of the FP64 pipe (1/64 of their rate on this GPU).
+__device__ __forceinline__ void jac_set(double& x, double v) { x = v; }
+__device__ __forceinline__ void jac_set(df32& x, double v) { x = df32(v); }
+__device__ __forceinline__ double jac_get(double x) { return x; }
+__device__ __forceinline__ double jac_get(df32 x) { return f2d_alu(x.hi) + f2d_alu(x.lo); }
+__device__ __forceinline__ double jac_lead(double x) { return x; }            // for tests and sums
+__device__ __forceinline__ double jac_lead(df32 x) { return f2d_alu(x.hi); }
+__device__ __forceinline__ bool jac_iszero(double x) { return x == 0.0; }
+__device__ __forceinline__ bool jac_iszero(df32 x) { return x.hi == 0.f; }
+__device__ __forceinline__ double jac_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ df32 jac_sqrt(df32 x) { return df_sqrt(x); }
+__device__ __forceinline__ double jac_abs(double x) { return fabs(x); }
+__device__ __forceinline__ df32 jac_abs(df32 x) { return x.hi < 0.f ? -x : x; }
+template <typename T> __device__ __forceinline__ T jac_one();
+template <> __device__ __forceinline__ double jac_one<double>() { return 1.0; }
+template <> __device__ __forceinline__ df32 jac_one<df32>() { return df32(1.0f, 0.f); }
+template <typename T> __device__ __forceinline__ T jac_zero();
+template <> __device__ __forceinline__ double jac_zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ df32 jac_zero<df32>() { return df32(0.f, 0.f); }
+// a rotation is skipped when |a_pq| <= JacEps::skip sqrt(|a_pp a_qq|); the sweeps stop when the
+// off-diagonal Frobenius norm squared is below JacEps::off of the whole (relative round-off level)
+template <typename T> struct JacEps;
+template <> struct JacEps<double> { static constexpr double skip = 1e-15, off = 1e-28; };
+template <> struct JacEps<df32> { static constexpr double skip = 1e-13, off = 1e-25; };
+
 // Cyclic Jacobi eigensolver of the symmetric n x n block of each molecule, one thread block per
 // molecule, rotations in parallel over disjoint index pairs (round-robin "circle" schedule).  The
 // rotation of (p, q) uses tau = (a_qq - a_pp)/(2 a_pq), t = sign(tau)/(|tau| + sqrt(1 + tau^2)),
 // c = 1/sqrt(1 + t^2), s = t c, and A <- J^T A J, V <- V J.  Eigenvalues ascending in eps, the
-// matching eigenvectors as the columns of Vout.  The matrix lives in shared memory when it fits,
-// otherwise in the global workspace Wk.
-__global__ void k_jacobi(const double* __restrict__ Ain, double* __restrict__ V, double* __restrict__ Vout,
-                         double* __restrict__ eps, const long long* __restrict__ ebase, Layout L, int use_smem,
-                         double* __restrict__ Wk, int max_sweeps, int* __restrict__ sweeps_out)
+// matching eigenvectors as the columns of Vout.  The matrix (element type T, 8 bytes) lives in
+// shared memory when it fits, otherwise in the global workspace Wk.  The eigenvectors accumulate
+// transposed in the global workspace Vt (row k = eigenvector k), so that the update of V's columns
+// p, q runs along contiguous rows.  Each warp takes whole rows (lanes along the row): no index
+// division anywhere in the sweeps.
+template <typename T>
+__global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Ain, T* __restrict__ Vt_ws,
+                                                double* __restrict__ Vout, double* __restrict__ eps,
+                                                const long long* __restrict__ ebase, Layout L, int use_smem,
+                                                T* __restrict__ Wk, int max_sweeps, int* __restrict__ sweeps_out)
 {
-    extern __shared__ __align__(16) double jsm[];
+    extern __shared__ __align__(16) unsigned char jsm_raw[];
     __shared__ double red[32];
     __shared__ int pp_[128], qq_[128];
-    __shared__ double cc_[128], ss_[128];
+    __shared__ T cc_[128], ss_[128];
     __shared__ int rotated;
     const int m = blockIdx.x;
     if (!L.active[m]) return;
     const int n = L.n[m];
     const long long o = L.base[m];
-    double* A = use_smem ? jsm : Wk + o;
+    T* A = use_smem ? reinterpret_cast<T*>(jsm_raw) : Wk + o;
+    T* Vt = Vt_ws + o;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int npad = n + (n & 1), half = npad / 2, rounds = npad - 1;
-    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
-        A[t] = Ain[o + t];
-        const int i = (int)(t / n), j = (int)(t % n);
-        V[o + t] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
+    const T one = jac_one<T>(), zero = jac_zero<T>();
     double nrm = 0.0;
-    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) nrm += A[t] * A[t];
-    nrm = block_sum(nrm, red);
+    for (int i = warp; i < n; i += nwarp)
+        for (int j = lane; j < n; j += 32) {
+            jac_set(A[i * n + j], Ain[o + (long long)i * n + j]);
+            Vt[i * n + j] = (i == j) ? one : zero;
+            const double a = jac_lead(A[i * n + j]);
+            nrm += a * a;
+        }
+    nrm = block_sum(nrm, red);   // (synchronises the block)
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         double off = 0.0;
-        for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
-            const int i = (int)(t / n), j = (int)(t % n);
-            if (i != j) off += A[t] * A[t];
-        }
+        for (int i = warp; i < n; i += nwarp)
+            for (int j = lane; j < n; j += 32) {
+                const double a = jac_lead(A[i * n + j]);
+                if (i != j) off += a * a;
+            }
         off = block_sum(off, red);
-        if (off <= 1e-28 * nrm || off == 0.0) break;
+        if (off <= JacEps<T>::off * nrm || off == 0.0) break;
         if (threadIdx.x == 0) rotated = 0;
         __syncthreads();
         for (int r = 0; r < rounds; ++r) {
@@ -372,15 +408,22 @@ __global__ void k_jacobi(const double* __restrict__ Ain, double* __restrict__ V,
                 if (k == 0) { a = rounds; b2 = r; }
                 else { a = (r + k) % rounds; b2 = (r - k + rounds) % rounds; }
                 const int p = min(a, b2), q = max(a, b2);
-                double c = 1.0, s = 0.0;
+                T c = one, s = zero;
                 if (q < n) {
-                    const double apq = A[(long long)p * n + q];
-                    const double app = A[(long long)p * n + p], aqq = A[(long long)q * n + q];
+                    const T apq = A[p * n + q];
+                    const T app = A[p * n + p], aqq = A[q * n + q];
+                    const double lpq = fabs(jac_lead(apq));
                     // rotate unless a_pq is negligible against the diagonal (round-off level)
-                    if (fabs(apq) > 1e-300 && fabs(apq) > 1e-15 * sqrt(fabs(app) * fabs(aqq))) {
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                    if (lpq > 1e-300 && lpq > JacEps<T>::skip * sqrt(fabs(jac_lead(app)) * fabs(jac_lead(aqq)))) {
+                        const T tau = (aqq - app) / (apq + apq);
+                        T t;
+                        if (fabs(jac_lead(tau)) > 1e15) {
+                            t = one / (tau + tau);   // t -> 1/(2 tau); tau^2 would overflow FP32
+                        } else {
+                            const T den = jac_abs(tau) + jac_sqrt(one + tau * tau);
+                            t = (jac_lead(tau) >= 0.0 ? one : -one) / den;
+                        }
+                        c = one / jac_sqrt(one + t * t);
                         s = t * c;
                         rotated = 1;
                     }
@@ -388,45 +431,47 @@ __global__ void k_jacobi(const double* __restrict__ Ain, double* __restrict__ V,
                 pp_[k] = p; qq_[k] = q; cc_[k] = c; ss_[k] = s;
             }
             __syncthreads();
-            // rows p, q:  row_p <- c row_p - s row_q,  row_q <- s row_p + c row_q
-            for (long long t = threadIdx.x; t < (long long)half * n; t += blockDim.x) {
-                const int k = (int)(t / n), j = (int)(t % n);
+            // rows p, q:  row_p <- c row_p - s row_q,  row_q <- s row_p + c row_q  (a warp per pair)
+            for (int k = warp; k < half; k += nwarp) {
                 const int p = pp_[k], q = qq_[k];
-                if (q >= n || ss_[k] == 0.0) continue;
-                const double c = cc_[k], s = ss_[k];
-                const double x = A[(long long)p * n + j], y = A[(long long)q * n + j];
-                A[(long long)p * n + j] = c * x - s * y;
-                A[(long long)q * n + j] = s * x + c * y;
+                if (q >= n || jac_iszero(ss_[k])) continue;
+                const T c = cc_[k], s = ss_[k];
+                for (int j = lane; j < n; j += 32) {
+                    const T x = A[p * n + j], y = A[q * n + j];
+                    A[p * n + j] = c * x - s * y;
+                    A[q * n + j] = s * x + c * y;
+                }
             }
             __syncthreads();
-            // columns p, q of A and of V
-            for (long long t = threadIdx.x; t < (long long)half * n; t += blockDim.x) {
-                const int k = (int)(t / n), i = (int)(t % n);
+            // columns p, q of A; rows p, q of V^T
+            for (int k = warp; k < half; k += nwarp) {
                 const int p = pp_[k], q = qq_[k];
-                if (q >= n || ss_[k] == 0.0) continue;
-                const double c = cc_[k], s = ss_[k];
-                const double x = A[(long long)i * n + p], y = A[(long long)i * n + q];
-                A[(long long)i * n + p] = c * x - s * y;
-                A[(long long)i * n + q] = s * x + c * y;
-                const double vx = V[o + (long long)i * n + p], vy = V[o + (long long)i * n + q];
-                V[o + (long long)i * n + p] = c * vx - s * vy;
-                V[o + (long long)i * n + q] = s * vx + c * vy;
+                if (q >= n || jac_iszero(ss_[k])) continue;
+                const T c = cc_[k], s = ss_[k];
+                for (int i = lane; i < n; i += 32) {
+                    const T x = A[i * n + p], y = A[i * n + q];
+                    A[i * n + p] = c * x - s * y;
+                    A[i * n + q] = s * x + c * y;
+                    const T vx = Vt[p * n + i], vy = Vt[q * n + i];
+                    Vt[p * n + i] = c * vx - s * vy;
+                    Vt[q * n + i] = s * vx + c * vy;
+                }
             }
             __syncthreads();
         }
         if (!rotated) break;
         __syncthreads();
     }
-    // eigenvalues ascending (rank by counting), eigenvectors permuted into Vout
+    // eigenvalues ascending (rank by counting), eigenvectors (rows of V^T) into the columns of Vout
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double ai = A[(long long)i * n + i];
+        const double ai = jac_get(A[i * n + i]);
         int rank = 0;
         for (int j = 0; j < n; ++j) {
-            const double aj = A[(long long)j * n + j];
+            const double aj = jac_get(A[j * n + j]);
             rank += (aj < ai) || (aj == ai && j < i);
         }
         eps[ebase[m] + rank] = ai;
-        for (int r = 0; r < n; ++r) Vout[o + (long long)r * n + rank] = V[o + (long long)r * n + i];
+        for (int r = 0; r < n; ++r) Vout[o + (long long)r * n + rank] = jac_get(Vt[i * n + r]);
     }
     if (threadIdx.x == 0 && sweeps_out) sweeps_out[m] = sweep;
 }
@@ -482,6 +527,9 @@ struct SCFState {
     Dev<unsigned char> active;
     int use_smem;
     size_t jac_smem;
+    // Fock matrices diagonalised in FP64 (the FP64 path) or double-float (reduced precision); the
+    // overlap matrix of the orthogonaliser always in FP64
+    bool fock_fp64 = true;
     Layout L;
     StreamGuard sg;   // the private stream: last member, so it is drained before the buffers are freed
 };
@@ -501,13 +549,23 @@ cudaError_t gemm(SCFState& st, bool transB, const double* A, const double* B, do
 cudaError_t jacobi_prepare(SCFState& st)
 {
     if (!st.use_smem) return cudaSuccess;
-    return cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st.jac_smem);
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st.jac_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_jacobi<df32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st.jac_smem);
 }
 
-cudaError_t jacobi(SCFState& st, const double* A, double* Vout)
+// Eigen-decomposition of the packed symmetric blocks A (eigenvectors to Vout, eigenvalues to eps).
+// fp64: FP64 arithmetic; otherwise double-float (the reduced-precision SCF's Fock matrices).  The
+// workspaces W2 and Wk hold 8-byte elements of either type.
+cudaError_t jacobi(SCFState& st, const double* A, double* Vout, bool fp64 = true)
 {
-    k_jacobi<<<st.nmol, 512, st.jac_smem, st.s>>>(A, st.W2.p, Vout, st.eps.p, st.ebase.p, st.L, st.use_smem,
-                                                  st.Wk.p, 40, st.sweeps.p);
+    if (fp64)
+        k_jacobi<double><<<st.nmol, 512, st.jac_smem, st.s>>>(A, st.W2.p, Vout, st.eps.p, st.ebase.p, st.L,
+                                                              st.use_smem, st.Wk.p, 40, st.sweeps.p);
+    else
+        k_jacobi<df32><<<st.nmol, 512, st.jac_smem, st.s>>>(A, reinterpret_cast<df32*>(st.W2.p), Vout, st.eps.p,
+                                                            st.ebase.p, st.L, st.use_smem,
+                                                            reinterpret_cast<df32*>(st.Wk.p), 40, st.sweeps.p);
     return cudaGetLastError();
 }
 
@@ -522,10 +580,10 @@ cudaError_t density_from_fock(SCFState& st, const double* Fin)
     if (st.warm) {
         if ((e = gemm(st, false, st.V.p, st.Vprev.p, st.W1.p, 0, 1.0)) != cudaSuccess) return e;          // F' Vprev
         if ((e = gemm(st, false, st.Vprev.p, st.W1.p, st.V.p, 0, 1.0, true)) != cudaSuccess) return e;    // Vprev^T F' Vprev
-        if ((e = jacobi(st, st.V.p, st.W1.p)) != cudaSuccess) return e;                                   // V_rel -> W1
+        if ((e = jacobi(st, st.V.p, st.W1.p, st.fock_fp64)) != cudaSuccess) return e;                     // V_rel -> W1
         if ((e = gemm(st, false, st.Vprev.p, st.W1.p, st.V.p, 0, 1.0)) != cudaSuccess) return e;          // V = Vprev V_rel
     } else {
-        if ((e = jacobi(st, st.V.p, st.W1.p)) != cudaSuccess) return e;                      // V -> W1
+        if ((e = jacobi(st, st.V.p, st.W1.p, st.fock_fp64)) != cudaSuccess) return e;       // V -> W1
         if ((e = cudaMemcpyAsync(st.V.p, st.W1.p, sizeof(double) * st.P, cudaMemcpyDeviceToDevice, st.s)) != cudaSuccess) return e;
         st.warm = true;
     }
@@ -740,8 +798,12 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         return MESS_ENOTIMPL;
     }
     SCFState st;
+    PhaseTimer tm((cudaStream_t)o.cuda_stream);
     mess_status su = scf_setup(st, b, (cudaStream_t)o.cuda_stream, diis_n, occ_in);
     if (su != MESS_OK) return su;
+    tm.s = st.s;
+    tm.mark(occ_in ? "scf (atoms): set-up" : "scf: set-up (pairs, one-electron matrices, orthogonaliser)");
+    st.fock_fp64 = o.prec == MESS_FP64;
     const size_t P = (size_t)st.P;
     const dim3 eg(64, b->nmol);
     std::vector<unsigned char> act(b->nmol, 1);
@@ -763,6 +825,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         MESS_CUDA_TRY(density_from_fock(st, st.H.p));
     }
     MESS_CUDA_TRY(jacobi_prepare(st));   // a nested SCF of the atomic densities may have changed it
+    tm.mark(occ_in ? "scf (atoms): initial density" : "scf: initial density");
 
     std::vector<double> Enuc(b->nmol), E(b->nmol);
     std::vector<int> iters(b->nmol, 0), conv(b->nmol, 0);
@@ -811,6 +874,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         mess_status js = mess_jk_ensure_bins(b, &jo);
         if (js != MESS_OK) return js;
     }
+    tm.mark("scf: quartet bins");
     // Kohn-Sham functionals: the grid and basis-function values (once per basis), E_xc and V_xc buffers
     Dev<double> Vxc, Exc;
     if (o.xc) {
@@ -936,6 +1000,11 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         MESS_CUDA_TRY(cudaEventSynchronize(hs.ev[k % 2]));
         remaining = hs.h[4 * (k % 2) + 1];
         err_mol = hs.h[4 * (k % 2) + 2];
+        if (tm.on) {
+            char lbl[96];
+            snprintf(lbl, sizeof lbl, "scf: iteration %d (%d molecules left after iteration %d)", it, remaining, k);
+            tm.mark(lbl);
+        }
         if (err_mol) break;
         if (remaining == 0) break;
         if (remaining * 2 < bins_cover && it < max_iter) {
@@ -950,6 +1019,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
             if (js != MESS_OK) return js;
             bins_cover = remaining;
             if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+            tm.mark("scf: quartet bins rebuilt");
         }
     }
     MESS_CUDA_TRY(cudaStreamSynchronize(st.s));
@@ -1012,6 +1082,7 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         if (js != MESS_OK) return js;
         MESS_CUDA_TRY(cudaMemcpyAsync(E.data(), st.E.p, sizeof(double) * b->nmol, cudaMemcpyDeviceToHost, st.s));
         MESS_CUDA_TRY(cudaStreamSynchronize(st.s));
+        tm.mark("scf: final energy (bins and build)");
         for (int m = 0; m < b->nmol; ++m) {
             if (!std::isfinite(E[m])) { mess_set_error("molecule %d: non-finite final energy", m); return MESS_ENUMERIC; }
             if (res) {
@@ -1343,8 +1414,10 @@ extern "C" mess_status mess_scf_batch(int nmol, mess_basis* const* bases, const 
 {
     if (nmol <= 0 || !bases || !res) { mess_set_error("bad batch arguments"); return MESS_EINVAL; }
     mess_basis* batch = nullptr;
+    PhaseTimer tm(opts ? (cudaStream_t)opts->cuda_stream : nullptr);
     mess_status st = mess_batch_basis(nmol, bases, &batch);
     if (st != MESS_OK) return st;
+    tm.mark("scf batch: batched basis");
     st = scf_run(batch, opts, res, nullptr, false);
     mess_free_basis(batch);
     delete batch;

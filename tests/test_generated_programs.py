@@ -282,15 +282,65 @@ def test_programs_read_only_written_slots(cls):
 
 
 @pytest.mark.parametrize("cls", CLASSES, ids=[GEN.tag(c) for c in CLASSES])
-def test_program_classes_stage_no_density_in_local_arrays(cls):
-    """The op-program classes digest with the density read through the read-only cache, never staged
-    in local arrays: a one-thread kernel that inlines the interpreter and also stages the density
-    blocks in local arrays was built with a stack frame smaller than its live arrays, and its
-    integrals came out as density values (the same source with the interpreter not inlined was
-    exact).  Straight-line classes stage the blocks, which then live in registers."""
-    _, info = GEN.emit_class(cls)
-    text = GEN.emit_digest(cls, unroll=(info["mode"] == "straight"))
-    staged = any(f"R {nm}[" in text for nm in ("Dab", "Dcd", "Dac", "Dad", "Dbc", "Dbd"))
-    assert staged == (info["mode"] == "straight"), (GEN.tag(cls), info["mode"])
+def test_interpreter_kernels_stage_no_density(cls):
+    """Where a one-thread kernel runs the op-program interpreter (the op-program classes, and the
+    double-float path of the larger straight-line classes), its digestion reads the density through
+    the read-only cache and never stages it in arrays: a one-thread kernel that inlined the
+    interpreter and also staged the density blocks in local arrays was built with a stack frame
+    smaller than its live arrays, and its integrals came out as density values (the same source with
+    the interpreter not inlined was exact).  The straight-line code stages the blocks in registers."""
+    t = GEN.tag(cls)
+    body, info = GEN.emit_class(cls)
+    text = GEN.emit_digests(cls, info)
+    staged = lambda txt: any(f"R {nm}[" in txt for nm in ("Dab", "Dcd", "Dac", "Dad", "Dbc", "Dbd"))
+    if info["mode"] == "program":
+        assert not staged(text)
+    elif GEN.df32_program(info):
+        assert f"eri_program<" in body and "std::is_same<R, df32>::value && G == 1" in body
+        ro = GEN.emit_digest(cls, unroll=False, name=f"digest_{t}_ro")
+        assert ro in text and not staged(ro)
+        assert f"if constexpr (std::is_same<R, df32>::value) digest_{t}_ro<R>(I, c, s);" in text
+    else:
+        assert "eri_program<" not in body and staged(text)
     src = open(os.path.join(ROOT, "paper_2406_03121_gb300", "csrc", "gen_eri.py")).read()
-    assert "emit_digest(cls, unroll=(info['mode'] == 'straight'))" in src
+    assert "dig = emit_digests(cls, info)" in src
+
+
+def _lane_split_visits(nb, nk, G, g, guard=True):
+    """The lane-split primitive loop of the straight-line kernels (G lanes, lane g), index logic only:
+    returns the (bra, ket) primitive indices lane g visits, or None if it runs past a step limit."""
+    b0, k0 = 0, 0
+    k1 = k0 + nk
+    b1 = b0 + (nb if nk > 0 else 0)
+    ib, ik, visits, steps = b0, k0 + g, [], 0
+    while ik >= k1 and (ib < b1 or not guard):
+        ik -= nk; ib += 1; steps += 1
+        if steps > 10000:
+            return None
+    while ib < b1:
+        visits.append((ib, ik))
+        ik += G
+        while ik >= k1 and (ib < b1 or not guard):
+            ik -= nk; ib += 1; steps += 1
+            if steps > 10000:
+                return None
+    return visits
+
+
+@pytest.mark.parametrize("G", [4, 8, 32])
+def test_lane_split_loop_terminates_and_covers(G):
+    """The lanes of a group visit every primitive quartet exactly once and always leave the loop, also
+    for a ket pair without primitives (nk = 0), where the unguarded index normalisation never ends."""
+    for nb in range(0, 5):
+        for nk in range(0, 7):
+            seen = []
+            for g in range(G):
+                v = _lane_split_visits(nb, nk, G, g)
+                assert v is not None, (nb, nk, G, g)
+                seen += v
+            assert sorted(seen) == [(b, k) for b in range(nb if nk else 0) for k in range(nk)]
+    assert _lane_split_visits(3, 0, G, 1, guard=False) is None     # what the guard prevents
+    _, info = GEN.emit_class(((1, 0), (1, 0)))
+    body, _ = GEN.emit_class_straight(((1, 0), (1, 0)))
+    assert body.count("while (ik >= k1 && ib < b1) { ik -= nk; ++ib; }") == 2
+    assert "b1 = b0 + ((live && nk > 0) ? P.pp_n[bp] : 0);" in body
