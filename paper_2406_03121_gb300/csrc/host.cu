@@ -273,9 +273,15 @@ mess_status mess_ensure_bins(mess_basis* b, double tau, double tau64, int split)
             // heavily contracted quartets: split the primitive loop over 8 lanes
             const bool straight = MESS_QCLASS[bp.qclass].straight != 0;
             const double avg = bp.total > 0 ? (double)bp.prim_quartets / (double)bp.total : 0.0;
-            // lanes per quartet: 8 for long primitive loops; 4 for medium loops of parts too small to
-            // fill the GPU one thread per quartet (measured: slower on parts of millions of quartets)
-            bp.G = !straight ? 1 : (avg >= 24.0 ? 8 : ((avg >= 6.0 && bp.total < (1LL << 18)) ? 4 : 1));
+            // lanes per quartet (the choice when the kernels are not autotuned).  FP64-class parts: 8 for
+            // long primitive loops, 4 for medium loops of parts too small to fill the GPU one thread per
+            // quartet.  Reduced-precision parts: one thread per quartet unless the part is small and its
+            // loops long - with G lanes only one lane in G digests, and for the small classes the
+            // digestion is most of the per-quartet work (measured on STO-3G alkanes, 81 primitive
+            // quartets per shell quartet: one thread per quartet 2.2x faster than 8 lanes).
+            if (!straight) bp.G = 1;
+            else if (fp64) bp.G = avg >= 24.0 ? 8 : ((avg >= 6.0 && bp.total < (1LL << 18)) ? 4 : 1);
+            else bp.G = (avg >= 6.0 && bp.total < (1LL << 15)) ? 4 : 1;
             // warp per quartet: always for the op-program classes; for small FP64 parts of the classes
             // with at least 40 VRR entries (too few quartets to fill the GPU one thread each:
             // measured better below about 2e6 quartets x VRR entries, worse above)
