@@ -202,7 +202,7 @@ mess_status mess_xc(const mess_basis* b, int xc, const double* D, double* Exc, d
  * mess_jk_build_device with opts->prec / schwarz_tau / fp64_tau, F = H + J - K/2, DIIS, the
  * diagonalisation of X^T F X (one thread block per molecule, cyclic Jacobi: FP64 for MESS_FP64,
  * double-float - about 48 significant bits, on the FP32 units - for MESS_MIXED / MESS_FP32) and
- * D = 2 C_occ C_occ^T.  The overlap matrix of X is always diagonalised in FP64.
+ * D = 2 C_occ C_occ^T; the overlap matrix of X in the same arithmetic.
  * With prec MESS_MIXED / MESS_FP32 the iterations use the reduced-precision builds and the reported
  * energy E_total is that of the final density from one full build in which the quartets above a ten
  * times lower split threshold (MESS_MIXED; every quartet for MESS_FP32) run in double-float
@@ -378,8 +378,9 @@ mess_status mess_mlp_features(const mess_basis* b, const double* D, float* X, fl
 mess_status mess_mlp_loss_grad(mess_mlp* m, long long nrows, const float* X, const float* T, const float* M,
                                double* loss, float* grad);
 /* Train on the converged densities of bases[0..nmol) (batched device SCF with opts scf), every
- * ordered atom pair one row, Adam (lr, beta 0.9 / 0.999) over shuffled batches of batch_rows rows for
- * `epochs` epochs; loss_out (nullable, epochs doubles) receives each epoch's mean loss. */
+ * ordered atom pair one row, Adam (beta 0.9 / 0.999) over shuffled batches of batch_rows rows for
+ * `epochs` epochs, the step size decaying from lr to 0 along a half cosine over all the steps;
+ * loss_out (nullable, epochs doubles) receives each epoch's mean loss. */
 mess_status mess_mlp_train(mess_mlp* m, int nmol, mess_basis* const* bases, const mess_scf_opts* scf, int epochs,
                            int batch_rows, double lr, double* loss_out);
 /* The network's density D0 (host n*n, symmetrised, before any diagonalisation) for one molecule. */

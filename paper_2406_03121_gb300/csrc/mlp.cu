@@ -772,6 +772,10 @@ extern "C" mess_status mess_mlp_train(mess_mlp* m, int nmol, mess_basis* const* 
     for (long long i = 0; i < rows; ++i) perm[i] = i;
     unsigned long long rs = 0x243F6A8885A308D3ull;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    // step size: half-cosine decay from lr to 0 over the run (the last epochs average out the
+    // mini-batch noise that a constant step leaves in the weights)
+    const long long steps_per_epoch = rows / br, total_steps = std::max(1LL, steps_per_epoch * epochs);
+    long long step = 0;
     for (int ep = 0; ep < epochs; ++ep) {
         for (long long i = rows - 1; i > 0; --i) {   // Fisher-Yates with an xorshift stream
             rs ^= rs << 13; rs ^= rs >> 7; rs ^= rs << 17;
@@ -791,8 +795,10 @@ extern "C" mess_status mess_mlp_train(mess_mlp* m, int nmol, mess_basis* const* 
             MESS_CUDA_TRY(backward(m, Tb.p, Mb.p, br, count, 0));
             m->step++;
             const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
-            k_adam<<<(MlpParams::N + 255) / 256, 256>>>(m->w.p, m->g.p, m->m1.p, m->m2.p, MlpParams::N, (float)lr, b1, b2,
-                                                      eps, c1, c2);
+            const double lr_t = lr * 0.5 * (1.0 + cos(M_PI * (double)step / (double)total_steps));
+            ++step;
+            k_adam<<<(MlpParams::N + 255) / 256, 256>>>(m->w.p, m->g.p, m->m1.p, m->m2.p, MlpParams::N, (float)lr_t, b1,
+                                                      b2, eps, c1, c2);
             MESS_CUDA_TRY(refresh_bf16(m, 0));
             double l = 0.0;
             MESS_CUDA_TRY(cudaMemcpy(&l, m->loss.p, sizeof(double), cudaMemcpyDeviceToHost));

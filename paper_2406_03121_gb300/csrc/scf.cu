@@ -79,6 +79,20 @@ __global__ void k_axpbypcz(double* out, double a, const double* X, double bb, co
     }
 }
 
+// W = 3/2 I - 1/2 M on each active molecule block (the Newton-Schulz step V <- V (3I - V^T V) / 2
+// that makes nearly orthonormal columns orthonormal to second order)
+__global__ void k_ns_factor(double* __restrict__ W, const double* __restrict__ M, Layout L)
+{
+    const int m = blockIdx.y;
+    if (!L.active[m]) return;
+    const int n = L.n[m];
+    const long long o = L.base[m];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+        const int i = t / n, j = t - i * n;
+        W[o + t] = (i == j ? 1.5 : 0.0) - 0.5 * M[o + t];
+    }
+}
+
 // E_m = 1/2 sum D (H + F)
 __global__ void k_energy(const double* __restrict__ D, const double* __restrict__ H, const double* __restrict__ F,
                          Layout L, double* __restrict__ E)
@@ -527,8 +541,8 @@ struct SCFState {
     Dev<unsigned char> active;
     int use_smem;
     size_t jac_smem;
-    // Fock matrices diagonalised in FP64 (the FP64 path) or double-float (reduced precision); the
-    // overlap matrix of the orthogonaliser always in FP64
+    // eigensolver arithmetic: FP64 (the FP64 path) or double-float (reduced precision), for the
+    // Fock matrices and the overlap matrix of the orthogonaliser alike
     bool fock_fp64 = true;
     Layout L;
     StreamGuard sg;   // the private stream: last member, so it is drained before the buffers are freed
@@ -681,9 +695,10 @@ static mess_status sad_density(mess_basis* b, const mess_scf_opts& o, double* D0
 // the given fractional occupations), every packed work matrix, the one-electron matrices S and
 // H = T + V, and the Loewdin orthogonaliser X = S^-1/2 (MESS_ENUMERIC if S is nearly singular).
 static mess_status scf_setup(SCFState& st, mess_basis* b, cudaStream_t caller, int diis_n,
-                             const std::vector<std::vector<double>>* occ_in)
+                             const std::vector<std::vector<double>>* occ_in, bool fp64_eig)
 {
     st.b = b;
+    st.fock_fp64 = fp64_eig;
     // The SCF runs on a private non-blocking stream (a CUDA graph cannot be captured on the legacy
     // default stream), ordered after the caller's stream; the call synchronises it before returning.
     {
@@ -767,7 +782,7 @@ static mess_status scf_setup(SCFState& st, mess_basis* b, cudaStream_t caller, i
     k_axpbypcz<<<eg, 256, 0, st.s>>>(st.H.p, 1.0, st.W1.p, 1.0, st.W2.p, 0.0, nullptr, st.L);   // H = T + V
     MESS_CUDA_TRY(cudaGetLastError());
     MESS_CUDA_TRY(jacobi_prepare(st));
-    MESS_CUDA_TRY(jacobi(st, st.S.p, st.V.p));                                        // S = U s U^T
+    MESS_CUDA_TRY(jacobi(st, st.S.p, st.V.p, st.fock_fp64));                          // S = U s U^T
     k_scale_cols<<<b->nmol, 256, 0, st.s>>>(st.V.p, st.eps.p, st.ebase.p, st.W1.p, st.L, st.smin.p);
     MESS_CUDA_TRY(cudaGetLastError());
     MESS_CUDA_TRY(gemm(st, true, st.W1.p, st.V.p, st.X.p, 0, 1.0));                 // X = U s^-1/2 U^T
@@ -799,11 +814,10 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
     }
     SCFState st;
     PhaseTimer tm((cudaStream_t)o.cuda_stream);
-    mess_status su = scf_setup(st, b, (cudaStream_t)o.cuda_stream, diis_n, occ_in);
+    mess_status su = scf_setup(st, b, (cudaStream_t)o.cuda_stream, diis_n, occ_in, o.prec == MESS_FP64);
     if (su != MESS_OK) return su;
     tm.s = st.s;
     tm.mark(occ_in ? "scf (atoms): set-up" : "scf: set-up (pairs, one-electron matrices, orthogonaliser)");
-    st.fock_fp64 = o.prec == MESS_FP64;
     const size_t P = (size_t)st.P;
     const dim3 eg(64, b->nmol);
     std::vector<unsigned char> act(b->nmol, 1);
@@ -1071,6 +1085,19 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         for (int m = 0; m < b->nmol; ++m) { act[m] = 1; b->active[m] = 1; }
         b->active_version++;
         MESS_CUDA_TRY(cudaMemcpyAsync(st.active.p, act.data(), b->nmol, cudaMemcpyHostToDevice, st.s));
+        if (!st.fock_fp64 && st.warm) {
+            // The double-float rotations are orthogonal to about 1e-14 each, and the warm-started
+            // eigenvectors carry that drift from iteration to iteration (V^T V - I of order 1e-11 at
+            // the end).  The energy is not stationary in that direction (a non-orthonormal C changes
+            // tr D S), so the density of the energy's build comes from eigenvectors made orthonormal
+            // again by one FP64 Newton-Schulz step, V <- V (3I - V^T V) / 2.
+            MESS_CUDA_TRY(gemm(st, false, st.Vprev.p, st.Vprev.p, st.W1.p, 0, 1.0, true));   // V^T V
+            k_ns_factor<<<eg, 256, 0, st.s>>>(st.W2.p, st.W1.p, st.L);
+            MESS_CUDA_TRY(cudaGetLastError());
+            MESS_CUDA_TRY(gemm(st, false, st.Vprev.p, st.W2.p, st.V.p, 0, 1.0));             // V (3I - V^T V) / 2
+            MESS_CUDA_TRY(gemm(st, false, st.X.p, st.V.p, st.C.p, 0, 1.0));                  // C = X V
+            MESS_CUDA_TRY(gemm(st, true, st.C.p, st.C.p, st.D.p, 1, 1.0));                   // D = C diag(occ) C^T
+        }
         mess_jk_opts jf = jo;
         jf.prec = MESS_MIXED;
         // ten times more of the largest quartets in FP64-class arithmetic than in the iterations
@@ -1275,7 +1302,7 @@ mess_status min_run(mess_basis* b, const mess_min_opts* opts, mess_scf_result* r
         return MESS_ENOTIMPL;
     }
     SCFState st;
-    mess_status su = scf_setup(st, b, (cudaStream_t)o.cuda_stream, 1, nullptr);
+    mess_status su = scf_setup(st, b, (cudaStream_t)o.cuda_stream, 1, nullptr, o.prec == MESS_FP64);
     if (su != MESS_OK) return su;
     const size_t P = (size_t)st.P;
     const int nmol = b->nmol;
