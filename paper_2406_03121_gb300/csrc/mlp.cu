@@ -30,6 +30,7 @@
 namespace {
 
 constexpr int DIN = MESS_MLP_DIN, WID = MESS_MLP_WIDTH, DOUT = MESS_MLP_DOUT, DOUT_PAD = 32;
+constexpr int MLP_MAX_SPLIT = 64;    // K slices of the split gradient GEMMs and column sums
 constexpr int NRBF = 32;
 
 struct MlpParams {   // offsets into the flat parameter vector
@@ -218,8 +219,10 @@ __global__ void k_symmetrise(double* __restrict__ D, const long long* __restrict
 // ------------------------------------------------------------------------------------ BF16 GEMM
 // C[m][n] (op)= sum_k A(m, k) B(k, n), A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn]
 // (BF16), FP32 accumulation on tensor cores (mma.sync m16n8k16).  64 x 64 block tile, 4 warps of
-// 32 x 32, K step 16.  gridDim.z splits K (then C is accumulated atomically).  Epilogue: + bias[n];
-// store FP32 to C (ldc) and optionally SiLU(C) as BF16 to Abf (ldc).
+// 32 x 32, K step 16.  gridDim.z splits K: slice z then stores its partial sums to part + z * pstride
+// (same layout as C), and k_sum_parts adds the slices in order z = 0, 1, ... (no atomics: training is
+// reproducible run to run).  Epilogue: + bias[n]; store FP32 to C (ldc) and optionally SiLU(C) as
+// BF16 to Abf (ldc).
 struct GemmArgs {
     const __nv_bfloat16* A;
     long long sam, sak;
@@ -230,7 +233,8 @@ struct GemmArgs {
     const float* bias;
     __nv_bfloat16* act;     // SiLU(C + bias) as BF16 (nullable)
     int M, N, K;
-    int atomic;             // 1: C += partial (split K), no epilogue
+    float* part;            // split K: per-slice partial sums (no epilogue); null: one slice
+    long long pstride;      // elements between slices of part
 };
 
 __device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
@@ -303,8 +307,8 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
                 const int c = n0 + wn + 8 * b + tig * 2 + (h & 1);
                 if (r >= g.M || c >= g.N) continue;
                 float v = acc[a][b][h];
+                if (g.part) { g.part[blockIdx.z * g.pstride + (long long)r * g.ldc + c] = v; continue; }
                 float* dst = g.C + (long long)r * g.ldc + c;
-                if (g.atomic) { atomicAdd(dst, v); continue; }
                 if (g.bias) v += g.bias[c];
                 *dst = v;
                 if (g.act) g.act[(long long)r * g.ldc + c] = __float2bfloat16(v / (1.f + __expf(-v)));
@@ -351,15 +355,39 @@ __global__ void k_silu_back(const float* __restrict__ dA, const float* __restric
     }
 }
 
-// column sums of a BF16 rows x cols matrix into g (FP32, atomic)
-__global__ void k_colsum(const __nv_bfloat16* __restrict__ X, long long rows, int cols, float* __restrict__ g)
+// out[i] = sum over slices z = 0 .. nz-1 (in that order) of part[z * pstride + i], for the M x N
+// entries i = r * ld + c
+__global__ void k_sum_parts(const float* __restrict__ part, int nz, long long pstride, int M, int N, long long ld,
+                            float* __restrict__ out)
 {
-    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
-    if (c >= cols) return;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)M * N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = (t / N) * ld + t % N;
+        float s = 0.f;
+        for (int z = 0; z < nz; ++z) s += part[z * pstride + i];
+        out[i] = s;
+    }
+}
+
+// column sums of a BF16 rows x cols matrix: block (x, y) sums the rows y, y + gridDim.y, ... of its 32
+// columns (its warps' shares added in warp order) into part[y * cols + c]; k_sum_parts then adds the
+// gridDim.y slices in order (no atomics)
+__global__ void k_colsum(const __nv_bfloat16* __restrict__ X, long long rows, int cols, float* __restrict__ part)
+{
+    __shared__ float ws[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (long long r = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += (long long)gridDim.y * (blockDim.x >> 5))
-        s += __bfloat162float(X[r * cols + c]);
-    atomicAdd(g + c, s);
+    if (c < cols)
+        for (long long r = (long long)blockIdx.y * nw + w; r < rows; r += (long long)gridDim.y * nw)
+            s += __bfloat162float(X[r * cols + c]);
+    ws[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && c < cols) {
+        float t = 0.f;
+        for (int k = 0; k < nw; ++k) t += ws[k][lane];
+        part[(long long)blockIdx.y * cols + c] = t;
+    }
 }
 
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1, float* __restrict__ m2,
@@ -392,6 +420,7 @@ struct mess_mlp {
     DevBuf<__nv_bfloat16> xb, a1, a2, dyb, dz2, dz1;
     DevBuf<float> z1, z2, y, da2, da1;
     DevBuf<double> loss;
+    DevBuf<float> part;                         // per-slice partial sums of the gradient reductions
 };
 
 namespace {
@@ -411,21 +440,30 @@ cudaError_t ensure_cap(mess_mlp* m, long long rows)
     if ((e = m->y.alloc(rows * DOUT_PAD)) != cudaSuccess) return e;
     if ((e = m->da2.alloc(rows * WID)) != cudaSuccess) return e;
     if ((e = m->da1.alloc(rows * WID)) != cudaSuccess) return e;
+    if (!m->part.p) {
+        const long long most = std::max<long long>({(long long)WID * WID, (long long)DIN * WID, (long long)WID * DOUT_PAD});
+        if ((e = m->part.alloc(MLP_MAX_SPLIT * most)) != cudaSuccess) return e;
+    }
     m->cap = rows;
     return cudaSuccess;
 }
 
+unsigned grid1(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 65535LL * 8); }
+
 cudaError_t gemm(const __nv_bfloat16* A, long long sam, long long sak, const __nv_bfloat16* B, long long sbk,
                  long long sbn, float* C, long long ldc, int M, int N, int K, const float* bias,
-                 __nv_bfloat16* act, int splitk, cudaStream_t s)
+                 __nv_bfloat16* act, int splitk, cudaStream_t s, float* part = nullptr)
 {
-    GemmArgs g{A, sam, sak, B, sbk, sbn, C, ldc, bias, act, M, N, K, splitk > 1 ? 1 : 0};
+    // split K only into a workspace of MLP_MAX_SPLIT slices of M x ldc (no epilogue then)
+    if (splitk > 1 && (!part || splitk > MLP_MAX_SPLIT || bias || act)) return cudaErrorInvalidValue;
+    const long long pstride = (long long)M * ldc;
+    GemmArgs g{A, sam, sak, B, sbk, sbn, C, ldc, bias, act, M, N, K, splitk > 1 ? part : nullptr, pstride};
     dim3 grid((N + 63) / 64, (M + 63) / 64, splitk);
     k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+    if (splitk > 1) k_sum_parts<<<grid1((long long)M * N), 256, 0, s>>>(part, splitk, pstride, M, N, ldc, C);
     return cudaGetLastError();
 }
 
-unsigned grid1(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 65535LL * 8); }
 
 // forward of `rows` rows whose FP32 descriptors are in X (device); output Y (rows x 32, FP32)
 cudaError_t forward(mess_mlp* m, const float* X, long long rows, cudaStream_t s)
@@ -452,25 +490,30 @@ cudaError_t backward(mess_mlp* m, const float* T, const float* M, long long rows
     k_loss<<<grid1(rows * DOUT_PAD), 256, 0, s>>>(m->y.p, T, M, rows, 1.0 / std::max(1.0, count), m->loss.p, m->dyb.p);
     const __nv_bfloat16* wb = m->wb.p;
     float* g = m->g.p;
-    const int split = (int)std::min<long long>(64, std::max<long long>(1, rows / 4096));
+    const int split = (int)std::min<long long>(MLP_MAX_SPLIT, std::max<long long>(1, rows / 4096));
+    float* part = m->part.p;
+    auto colsum = [&](const __nv_bfloat16* X, int cols, float* out) {
+        k_colsum<<<dim3((cols + 31) / 32, MLP_MAX_SPLIT), 256, 0, s>>>(X, rows, cols, part);
+        k_sum_parts<<<grid1(cols), 256, 0, s>>>(part, MLP_MAX_SPLIT, cols, 1, cols, cols, out);
+    };
     // layer 3: dW3 = A2^T dY, db3 = sum dY, dA2 = dY W3^T
     if ((e = gemm(m->a2.p, 1, WID, m->dyb.p, DOUT_PAD, 1, g + MlpParams::W3, DOUT_PAD, WID, DOUT_PAD, (int)rows,
-                  nullptr, nullptr, split, s)) != cudaSuccess) return e;
-    k_colsum<<<dim3(1, 64), 256, 0, s>>>(m->dyb.p, rows, DOUT_PAD, g + MlpParams::B3);
+                  nullptr, nullptr, split, s, part)) != cudaSuccess) return e;
+    colsum(m->dyb.p, DOUT_PAD, g + MlpParams::B3);
     if ((e = gemm(m->dyb.p, DOUT_PAD, 1, wb + MlpParams::W3, 1, DOUT_PAD, m->da2.p, WID, (int)rows, WID, DOUT_PAD,
                   nullptr, nullptr, 1, s)) != cudaSuccess) return e;
     k_silu_back<<<grid1(rows * WID), 256, 0, s>>>(m->da2.p, m->z2.p, m->dz2.p, rows * WID);
     // layer 2
     if ((e = gemm(m->a1.p, 1, WID, m->dz2.p, WID, 1, g + MlpParams::W2, WID, WID, WID, (int)rows,
-                  nullptr, nullptr, split, s)) != cudaSuccess) return e;
-    k_colsum<<<dim3(WID / 32, 64), 256, 0, s>>>(m->dz2.p, rows, WID, g + MlpParams::B2);
+                  nullptr, nullptr, split, s, part)) != cudaSuccess) return e;
+    colsum(m->dz2.p, WID, g + MlpParams::B2);
     if ((e = gemm(m->dz2.p, WID, 1, wb + MlpParams::W2, 1, WID, m->da1.p, WID, (int)rows, WID, WID,
                   nullptr, nullptr, 1, s)) != cudaSuccess) return e;
     k_silu_back<<<grid1(rows * WID), 256, 0, s>>>(m->da1.p, m->z1.p, m->dz1.p, rows * WID);
     // layer 1
     if ((e = gemm(m->xb.p, 1, DIN, m->dz1.p, WID, 1, g + MlpParams::W1, WID, DIN, WID, (int)rows,
-                  nullptr, nullptr, split, s)) != cudaSuccess) return e;
-    k_colsum<<<dim3(WID / 32, 64), 256, 0, s>>>(m->dz1.p, rows, WID, g + MlpParams::B1);
+                  nullptr, nullptr, split, s, part)) != cudaSuccess) return e;
+    colsum(m->dz1.p, WID, g + MlpParams::B1);
     return cudaGetLastError();
 }
 

@@ -79,20 +79,6 @@ __global__ void k_axpbypcz(double* out, double a, const double* X, double bb, co
     }
 }
 
-// W = 3/2 I - 1/2 M on each active molecule block (the Newton-Schulz step V <- V (3I - V^T V) / 2
-// that makes nearly orthonormal columns orthonormal to second order)
-__global__ void k_ns_factor(double* __restrict__ W, const double* __restrict__ M, Layout L)
-{
-    const int m = blockIdx.y;
-    if (!L.active[m]) return;
-    const int n = L.n[m];
-    const long long o = L.base[m];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
-        const int i = t / n, j = t - i * n;
-        W[o + t] = (i == j ? 1.5 : 0.0) - 0.5 * M[o + t];
-    }
-}
-
 // E_m = 1/2 sum D (H + F)
 __global__ void k_energy(const double* __restrict__ D, const double* __restrict__ H, const double* __restrict__ F,
                          Layout L, double* __restrict__ E)
@@ -1085,19 +1071,6 @@ mess_status scf_run(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* r
         for (int m = 0; m < b->nmol; ++m) { act[m] = 1; b->active[m] = 1; }
         b->active_version++;
         MESS_CUDA_TRY(cudaMemcpyAsync(st.active.p, act.data(), b->nmol, cudaMemcpyHostToDevice, st.s));
-        if (!st.fock_fp64 && st.warm) {
-            // The double-float rotations are orthogonal to about 1e-14 each, and the warm-started
-            // eigenvectors carry that drift from iteration to iteration (V^T V - I of order 1e-11 at
-            // the end).  The energy is not stationary in that direction (a non-orthonormal C changes
-            // tr D S), so the density of the energy's build comes from eigenvectors made orthonormal
-            // again by one FP64 Newton-Schulz step, V <- V (3I - V^T V) / 2.
-            MESS_CUDA_TRY(gemm(st, false, st.Vprev.p, st.Vprev.p, st.W1.p, 0, 1.0, true));   // V^T V
-            k_ns_factor<<<eg, 256, 0, st.s>>>(st.W2.p, st.W1.p, st.L);
-            MESS_CUDA_TRY(cudaGetLastError());
-            MESS_CUDA_TRY(gemm(st, false, st.Vprev.p, st.W2.p, st.V.p, 0, 1.0));             // V (3I - V^T V) / 2
-            MESS_CUDA_TRY(gemm(st, false, st.X.p, st.V.p, st.C.p, 0, 1.0));                  // C = X V
-            MESS_CUDA_TRY(gemm(st, true, st.C.p, st.C.p, st.D.p, 1, 1.0));                   // D = C diag(occ) C^T
-        }
         mess_jk_opts jf = jo;
         jf.prec = MESS_MIXED;
         // ten times more of the largest quartets in FP64-class arithmetic than in the iterations
