@@ -334,7 +334,7 @@ def _mlp_section(mess, args):
     kw = dict(prec="mixed", split_df32=True)
     net = mess.MLP(seed=3)
     t0 = time.perf_counter()
-    losses = net.train(train, epochs=40, batch_rows=8192, lr=2e-3, **kw)
+    losses = net.train(train, epochs=40, batch_rows=2048, lr=5e-3, **kw)
     t_train = time.perf_counter() - t0
     out = {"workload": f"train: {len(train)} alkanes n = 1..8 (seed 2004, labels = converged densities of the "
                        f"library's own SCF); test: {len(test)} alkanes n = 9..12 (seed 2005); STO-3G",

@@ -61,7 +61,7 @@ def test_training_gains_over_the_plain_guesses(mess, tmp_path):
     train = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(400, 1, 6, 2004)]
     test = [mess.Basis.from_molecule(m, sto) for m in mi.alkane_batch(16, 7, 8, 2005)]
     net = mess.MLP(seed=3)
-    losses = net.train(train, epochs=40, batch_rows=4096, lr=2e-3, prec="mixed", split_df32=True)
+    losses = net.train(train, epochs=100, batch_rows=2048, lr=5e-3, prec="mixed", split_df32=True)
     assert losses[-1] < 0.25 * losses[0]
     w = str(tmp_path / "guess.bin")
     net.save(w)
