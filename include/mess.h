@@ -221,11 +221,25 @@ mess_status mess_scf(const mess_basis* b, const mess_scf_opts* opts, mess_scf_re
  *   dE/dA_x = sum_{m on A, n} [2 D_mn (dm|h|n) + D_mn (2 J'_mn - K'_mn) - 2 W_mn (dm|n)]
  *             - 2 sum_{m,n} D_mn (dm|V_A|n) + dE_nuc/dA_x,
  * dm the derivative of basis function m with respect to its own centre, J'_mn = sum_ls (dm n|l s) D_ls,
- * K'_mn = sum_ls (dm l|n s) D_ls, W = D F D / 2, V_A the attraction of nucleus A.  Single-molecule
- * bases with shells up to p (STO-3G, 6-31G: the derivative of a d shell needs f functions), xc = 0.
- * grad: natom x 3 doubles (hartree/bohr); res (nullable): the SCF result.  Errors: as mess_scf;
- * MESS_ENOTIMPL (d shells, xc != 0). */
+ * K'_mn = sum_ls (dm l|n s) D_ls, W = D F D / 2, V_A the attraction of nucleus A.  That analytic form
+ * covers single-molecule bases with shells up to p (STO-3G, 6-31G) and xc = 0.  For bases with d
+ * shells (whose derivatives need f functions) or xc != 0 this call returns the numerical form of
+ * mess_gradient_numerical instead.  grad: natom x 3 doubles (hartree/bohr); res (nullable): the SCF
+ * result.  Errors: as mess_scf; MESS_EINVAL (batch bases). */
 mess_status mess_gradient(const mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* grad);
+
+/* Nuclear gradient as the derivative of the SCF energy taken numerically (the paper differentiates
+ * the energy, Secs. 1 and 4): runs mess_scf with opts for res, then one batched SCF (mess_scf_batch,
+ * the paper's batching over conformations, Sec. 5.2) of the 12 natom geometries with one atom moved
+ * by k h along one axis, k = 2, 1, -1, -2, h = 1e-3 bohr, in FP64 whatever opts->prec (the other
+ * options as given: converge tightly, e.g. conv_E 1e-12 and conv_comm 1e-10, for gradients good to
+ * 1e-8), and the fourth-order central difference
+ *   dE/dR = [-E(R + 2h) + 8 E(R + h) - 8 E(R - h) + E(R - 2h)] / (12 h)
+ * (truncation error of order h^4).  Any shells, Hartree-Fock or Kohn-Sham (opts->xc).  Single-molecule
+ * bases of at most 256 functions.  grad: natom x 3 doubles (hartree/bohr); res (nullable): the SCF
+ * result at R.  Errors: as mess_scf and mess_scf_batch; MESS_EINVAL (batch bases). */
+mess_status mess_gradient_numerical(const mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res,
+                                    double* grad);
 
 /* Batched SCF over many molecules (the paper's vmap over conformers, Sec. 5.2): every molecule of
  * bases[0..nmol) (single-molecule bases, any sizes) in the same kernel launches - the J/K kernels

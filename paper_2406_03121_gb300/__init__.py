@@ -29,7 +29,7 @@ EXPORTED = [
     "mess_basis_create", "mess_basis_nbf", "mess_basis_nshell", "mess_basis_nelectron",
     "mess_basis_destroy", "mess_overlap", "mess_kinetic", "mess_nuclear", "mess_one_e_device",
     "mess_nuclear_repulsion", "mess_jk_build", "mess_jk_build_device", "mess_jk_build_static", "mess_eri_tensor",
-    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_minimise", "mess_minimise_batch", "mess_xc", "mess_gradient", "mess_jk_profile", "mess_jk_autotune", "mess_jk_set_variant",
+    "mess_schwarz", "mess_scf", "mess_scf_batch", "mess_minimise", "mess_minimise_batch", "mess_xc", "mess_gradient", "mess_gradient_numerical", "mess_jk_profile", "mess_jk_autotune", "mess_jk_set_variant",
     "mess_jk_get_tuning", "mess_jk_set_tuning", "mess_boys_grid", "mess_profiler_range", "mess_fma_peak",
     "mess_last_error",
     "mess_mlp_num_params", "mess_mlp_create", "mess_mlp_destroy", "mess_mlp_get_params", "mess_mlp_set_params",
@@ -130,6 +130,8 @@ mess_minimise_batch = _sig("mess_minimise_batch", ctypes.c_int,
                             ctypes.POINTER(mess_scf_result), _DP])
 mess_gradient = _sig("mess_gradient", ctypes.c_int,
                      [_P, ctypes.POINTER(mess_scf_opts), ctypes.POINTER(mess_scf_result), _DP])
+mess_gradient_numerical = _sig("mess_gradient_numerical", ctypes.c_int,
+                               [_P, ctypes.POINTER(mess_scf_opts), ctypes.POINTER(mess_scf_result), _DP])
 mess_xc = _sig("mess_xc", ctypes.c_int, [_P, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_longlong)])
 mess_jk_profile = _sig("mess_jk_profile", ctypes.c_int,
                        [_P, _P, _P, _P, ctypes.POINTER(mess_jk_opts), ctypes.POINTER(mess_jk_part), ctypes.c_int,
@@ -347,12 +349,14 @@ class Basis:
                "mess_jk_profile")
         return [parts[i].as_dict() for i in range(n.value)]
 
-    def gradient(self, **scf_kw):
-        """SCF energy and nuclear gradient (natom x 3, hartree/bohr) (see mess_gradient)."""
+    def gradient(self, numerical=False, **scf_kw):
+        """SCF energy and nuclear gradient (natom x 3, hartree/bohr): mess_gradient (analytic where it
+        applies), or mess_gradient_numerical with numerical=True."""
         o = scf_opts(**scf_kw)
         r = mess_scf_result()
         g = np.zeros((len(self.Z), 3))
-        _check(mess_gradient(self._h, ctypes.byref(o), ctypes.byref(r), _dptr(g)), "mess_gradient")
+        fn, name = (mess_gradient_numerical, "mess_gradient_numerical") if numerical else (mess_gradient, "mess_gradient")
+        _check(fn(self._h, ctypes.byref(o), ctypes.byref(r), _dptr(g)), name)
         return r.as_dict(), g
 
     def xc(self, D, kind="lda"):

@@ -132,6 +132,56 @@ __global__ void k_energy_weighted(const double* __restrict__ D, const double* __
 
 }  // namespace
 
+// step of the central differences of the numerical gradient, bohr
+#define MESS_GRAD_STEP 1e-3
+
+extern "C" mess_status mess_gradient_numerical(const mess_basis* bc, const mess_scf_opts* opts,
+                                               mess_scf_result* res, double* grad)
+{
+    mess_basis* b = const_cast<mess_basis*>(bc);
+    if (!b || !grad) { mess_set_error("null argument"); return MESS_EINVAL; }
+    if (b->nmol != 1) { mess_set_error("mess_gradient_numerical: single-molecule bases only"); return MESS_EINVAL; }
+    mess_scf_opts o{};
+    if (opts) o = *opts;
+    mess_scf_result r{};
+    mess_status st = mess_scf(b, &o, &r, nullptr);
+    if (res) *res = r;
+    if (st != MESS_OK) return st;
+    // the 12 natom displaced geometries R + k h e_(atom, axis), k = 2, 1, -1, -2, as one batch
+    const int na = b->natom;
+    const double h = MESS_GRAD_STEP;
+    const int ks[4] = {2, 1, -1, -2};
+    std::vector<mess_basis*> disp;
+    disp.reserve((size_t)12 * na);
+    struct FreeAll {
+        std::vector<mess_basis*>& v;
+        ~FreeAll() { for (mess_basis* d : v) { mess_free_basis(d); delete d; } }
+    } free_all{disp};
+    for (int a = 0; a < na; ++a)
+        for (int x = 0; x < 3; ++x)
+            for (int k : ks) {
+                mess_basis* d = nullptr;
+                st = mess_displaced_basis(b, a, x, k * h, &d);
+                if (st != MESS_OK) return st;
+                disp.push_back(d);
+            }
+    // the differences resolve 1e-9 hartree/bohr only with FP64 energies: the displaced SCFs run in
+    // FP64 whatever opts->prec
+    mess_scf_opts od = o;
+    od.prec = MESS_FP64;
+    std::vector<mess_scf_result> rr(disp.size());
+    st = mess_scf_batch((int)disp.size(), disp.data(), &od, rr.data());
+    if (st != MESS_OK) return st;
+    for (int a = 0; a < na; ++a)
+        for (int x = 0; x < 3; ++x) {
+            const mess_scf_result* e = rr.data() + 4 * (3 * a + x);
+            const double g = (-e[0].E_total + 8.0 * e[1].E_total - 8.0 * e[2].E_total + e[3].E_total) / (12.0 * h);
+            if (!std::isfinite(g)) { mess_set_error("mess_gradient_numerical: non-finite gradient"); return MESS_ENUMERIC; }
+            grad[3 * a + x] = g;
+        }
+    return MESS_OK;
+}
+
 extern "C" mess_status mess_gradient(const mess_basis* bc, const mess_scf_opts* opts, mess_scf_result* res,
                                      double* grad)
 {
@@ -140,12 +190,12 @@ extern "C" mess_status mess_gradient(const mess_basis* bc, const mess_scf_opts* 
     if (b->nmol != 1) { mess_set_error("mess_gradient: single-molecule bases only"); return MESS_EINVAL; }
     mess_scf_opts o{};
     if (opts) o = *opts;
-    if (o.xc != 0) { mess_set_error("mess_gradient: Hartree-Fock only (xc = 0)"); return MESS_ENOTIMPL; }
+    // the analytic form covers Hartree-Fock with shells up to p (the derivative of a d shell needs f
+    // functions); otherwise the numerical form
+    bool analytic = o.xc == 0;
     for (const HostShell& s : b->shells)
-        if (s.l + 1 > MESS_LMAX) {
-            mess_set_error("mess_gradient: shells up to p (the derivative of a d shell needs f functions)");
-            return MESS_ENOTIMPL;
-        }
+        if (s.l + 1 > MESS_LMAX) analytic = false;
+    if (!analytic) return mess_gradient_numerical(bc, opts, res, grad);
     const int n = b->nbf, na = b->natom;
     std::vector<double> Dh((size_t)n * n);
     mess_scf_result r{};

@@ -904,6 +904,25 @@ mess_status mess_derivative_basis(const mess_basis* b, mess_basis** out, std::ve
     return MESS_OK;
 }
 
+mess_status mess_displaced_basis(const mess_basis* b, int atom, int axis, double dx, mess_basis** out)
+{
+    *out = nullptr;
+    if (b->nmol != 1 || atom < 0 || atom >= b->natom || axis < 0 || axis > 2) {
+        mess_set_error("displaced basis: bad arguments");
+        return MESS_EINVAL;
+    }
+    mess_basis* d = new (std::nothrow) mess_basis();
+    if (!d) { mess_set_error("host allocation failed"); return MESS_ENOMEM; }
+    std::vector<double> xyz(b->xyz);
+    xyz[3 * atom + axis] += dx;
+    std::vector<HostShell> sh(b->shells);
+    for (HostShell& s : sh)
+        if (s.atom == atom) s.R[axis] += dx;
+    add_molecule(d, b->Z, xyz, sh);
+    *out = d;
+    return MESS_OK;
+}
+
 mess_status mess_atoms_basis(const mess_basis* b, std::vector<int>& elements, mess_basis** out)
 {
     elements.clear();

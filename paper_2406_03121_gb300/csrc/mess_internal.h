@@ -209,6 +209,9 @@ mess_status mess_batch_basis(int nmol, const mess_basis* const* bases, mess_basi
 void mess_free_basis(mess_basis* b);
 // one single-atom molecule (at the origin) per distinct element of b; elements[e] = Z of molecule e
 mess_status mess_atoms_basis(const mess_basis* b, std::vector<int>& elements, mess_basis** out);
+// A host-only copy of a single-molecule basis with one atom (its nucleus and its shells) moved by dx
+// bohr along axis (0 x, 1 y, 2 z); its device data are built on first use like any basis's.
+mess_status mess_displaced_basis(const mess_basis* b, int atom, int axis, double dx, mess_basis** out);
 // batched SCF on an internal batch basis, final densities into dD (device, packed) (scf.cu)
 mess_status mess_scf_batch_density(mess_basis* b, const mess_scf_opts* opts, mess_scf_result* res, double* dD);
 // exchange-correlation (xc.cu): the grid and basis-function values of b (once), then for a packed
