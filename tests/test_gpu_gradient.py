@@ -56,3 +56,27 @@ def test_numerical_gradient_matches_the_analytic_one(mess):
     assert abs(ra["E_total"] - rn["E_total"]) <= 1e-9
     print("ch4_631g max |numerical - analytic| =", np.abs(gn - ga).max())
     assert np.abs(gn - ga).max() <= 1e-7
+
+
+def test_kohn_sham_gradient_matches_the_oracle(mess, oracle_mod):
+    """LDA on a distorted H2O in STO-3G: mess_gradient takes the numerical form (one batched Kohn-Sham
+    SCF of the 36 displaced geometries, each on its own atom-centred grid), against the fourth-order
+    central difference of the oracle's Kohn-Sham energy on its own grid."""
+    from oracle import dft
+    mol = _distorted(mi.h2o(), 8)
+    path = mi.basis_path("sto-3g")
+    g = mess.Basis.from_molecule(mol, path)
+    r, grad = g.gradient(prec="fp64", xc="lda", conv_E=1e-12, conv_comm=1e-10)
+    assert r["converged"] == 1
+    h = 1e-3
+    ref = np.zeros_like(mol.xyz)
+    for a in range(len(mol.Z)):
+        for x in range(3):
+            e = []
+            for k in (2, 1, -1, -2):
+                p = mol.xyz.copy()
+                p[a, x] += k * h
+                e.append(dft.ks_scf(oracle_mod.make_basis(mol.Z, p, path), "lda", conv_E=1e-12, conv_comm=1e-10)[0])
+            ref[a, x] = (-e[0] + 8.0 * e[1] - 8.0 * e[2] + e[3]) / (12.0 * h)
+    print("h2o_sto3g_lda max |dG| =", np.abs(grad - ref).max())
+    assert np.abs(grad - ref).max() <= 1e-6
